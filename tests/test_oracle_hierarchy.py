@@ -1,0 +1,218 @@
+"""Pins of the oracle's aggregation (Algorithm 2), prolongator (Sec. 2.2), Galerkin
+product (Sec. 2.1) and multi-sweep hierarchy (Sec. 5) against library products,
+closed forms and invariants (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from paper_1810_04221_gb300 import problems as P
+
+
+def _P_matrix(agg, p, nc):
+    n = len(agg)
+    return sp.csr_matrix((p, (np.arange(n), agg)), shape=(n, nc))
+
+
+def _one_sweep(rp, ci, val, v):
+    w = oracle.edge_weights(rp, ci, val, v)
+    mate = oracle.greedy_match(rp, ci, w)
+    agg, nc, npairs, nsing = oracle.aggregate(mate)
+    p, vc = oracle.prolongator(agg, nc, v)
+    return mate, agg, nc, npairs, nsing, p, vc
+
+
+# ------------------------------------------------------------ aggregation ----
+
+@pytest.mark.parametrize("seed", range(4))
+def test_aggregation_counts_and_order(seed):
+    rp, ci, val = P.random_spd(3000, 6.0, seed=seed, ties=seed % 2 == 1)
+    v = np.random.default_rng(seed).uniform(0.5, 2, 3000)
+    mate, agg, nc, npairs, nsing, p, vc = _one_sweep(rp, ci, val, v)
+    assert nc == npairs + nsing
+    assert npairs == int(np.sum(mate >= 0)) // 2
+    # every aggregate is a matched pair or a singleton
+    members = [[] for _ in range(nc)]
+    for i, a in enumerate(agg):
+        members[a].append(i)
+    for I, m in enumerate(members):
+        assert len(m) in (1, 2)
+        if len(m) == 2:
+            assert mate[m[0]] == m[1]
+        else:
+            assert mate[m[0]] < 0
+    # ids follow the smallest member (U scanned in ascending order)
+    firsts = [m[0] for m in members]
+    assert firsts == sorted(firsts)
+
+
+def test_aggregation_no_edges():
+    mate = -np.ones(7, np.int32)
+    agg, nc, npairs, nsing = oracle.aggregate(mate)
+    assert nc == 7 and npairs == 0 and nsing == 7 and np.array_equal(agg, np.arange(7))
+
+
+# ------------------------------------------------------------ prolongator ----
+
+@pytest.mark.parametrize("seed", range(3))
+def test_prolongator_orthonormal_and_reproduces_v(seed):
+    rp, ci, val = P.random_spd(2000, 5.0, seed=seed)
+    v = np.random.default_rng(seed).uniform(-2, 2, 2000)
+    v[::97] = 0.0  # zero entries exercise the singleton special case
+    mate, agg, nc, _, _, p, vc = _one_sweep(rp, ci, val, v)
+    Pm = _P_matrix(agg, p, nc)
+    PtP = (Pm.T @ Pm).toarray()
+    assert np.abs(PtP - np.eye(nc)).max() < 1e-15 * 4
+    assert np.abs(Pm @ vc - v).max() <= 1e-15 * np.abs(v).max() * 4
+    assert np.abs(Pm.T @ v - vc).max() <= 1e-15 * np.abs(v).max() * 4
+
+
+# -------------------------------------------------------------- Galerkin ----
+
+@pytest.mark.parametrize("kind,seed", [("rand", 0), ("rand", 1), ("ties", 2), ("diff", 3), ("zeros", 4)])
+def test_galerkin_vs_dense_product(kind, seed):
+    if kind == "diff":
+        rp, ci, val = P.lognormal_diffusion(10, seed=seed)
+        n = len(rp) - 1
+        v = np.ones(n)
+    else:
+        n = 1500
+        rp, ci, val = P.random_spd(n, 6.0, seed=seed, ties=kind == "ties",
+                                   explicit_zeros=0.2 if kind == "zeros" else 0.0)
+        v = np.random.default_rng(seed).uniform(0.5, 2, n)
+    mate, agg, nc, _, _, p, vc = _one_sweep(rp, ci, val, v)
+    rpc, cic, valc = oracle.galerkin(rp, ci, val, agg, nc, p)
+    assert oracle.check_csr(rpc, cic)
+    A = P.to_scipy(rp, ci, val)
+    Pm = _P_matrix(agg, p, nc)
+    dense = (Pm.T @ A @ Pm).toarray()
+    got = sp.csr_matrix((valc, cic, rpc), shape=(nc, nc)).toarray()
+    scale = np.abs(val).max()
+    assert np.abs(got - dense).max() <= 1e-14 * scale
+    # pattern = every (I, J) hit by a stored fine entry (structural zeros kept)
+    pat = sp.csr_matrix((np.ones_like(val), ci, rp), shape=(n, n))
+    B = sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, nc))
+    hit = (B.T @ pat @ B).tocsr()
+    hit.sort_indices()
+    assert np.array_equal(hit.indptr, rpc) and np.array_equal(hit.indices, cic)
+    # bit symmetry of A_c and A_c v_c = P^T (A v)
+    assert oracle.check_symmetric(rpc, cic, valc)
+    Ac = sp.csr_matrix((valc, cic, rpc), shape=(nc, nc))
+    lhs, rhs = Ac @ vc, Pm.T @ (A @ v)
+    assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(rhs).max()
+
+
+def test_galerkin_spd_by_cholesky():
+    rp, ci, val = P.random_spd(800, 6.0, seed=11)
+    v = np.ones(800)
+    mate, agg, nc, _, _, p, vc = _one_sweep(rp, ci, val, v)
+    rpc, cic, valc = oracle.galerkin(rp, ci, val, agg, nc, p)
+    Ac = sp.csr_matrix((valc, cic, rpc), shape=(nc, nc)).toarray()
+    np.linalg.cholesky(Ac)  # raises if not s.p.d.
+
+
+def test_galerkin_binary_p_row_sums():
+    # with a binary P (p = 1) the coarse row sums equal P^T (A 1): A_c 1 = P^T A 1
+    rp, ci, val = P.random_spd(1000, 5.0, seed=5)
+    mate, agg, nc, _, _, _, _ = _one_sweep(rp, ci, val, np.ones(1000))
+    ones = np.ones(1000)
+    rpc, cic, valc = oracle.galerkin(rp, ci, val, agg, nc, ones)
+    Ac = sp.csr_matrix((valc, cic, rpc), shape=(nc, nc))
+    Bm = _P_matrix(agg, ones, nc)
+    lhs = Ac @ np.ones(nc)
+    rhs = Bm.T @ (P.to_scipy(rp, ci, val) @ ones)
+    assert np.abs(lhs - rhs).max() <= 1e-13 * np.abs(rhs).max()
+
+
+# ------------------------------------------------------------- hierarchy ----
+
+def test_hierarchy_poisson2d_closed_form():
+    """64^2 Poisson, v = 1, 2 sweeps per level: 2x2 blocks on every level,
+    A^k = 2^{-k} L_5 on (64/2^k)^2, v_k = 2^k, n = 4096, 1024, 256, 64, 16."""
+    rp, ci, val = P.poisson2d(64)
+    H = oracle.Hierarchy(rp, ci, val, np.ones(4096), sweeps=2, coarse_max=40)
+    assert H.nl == 5
+    ns = [H.level_n(k) for k in range(5)]
+    zs = [H.level_nnz(k) for k in range(5)]
+    assert ns == [4096, 1024, 256, 64, 16]
+    assert zs == [5 * m * m - 4 * m for m in (64, 32, 16, 8, 4)]
+    vc, cr = H.stats()
+    assert abs(vc - (20224 + 4992 + 1216 + 288 + 64) / 20224) < 1e-15
+    assert abs(cr - 16.0 / 5.0) < 1e-15  # (1/nl) * 4 ratios of 4
+    for k in range(1, 5):
+        L = H.level(k)
+        m = 64 >> k
+        ref = P.to_scipy(*P.poisson2d(m)) * (0.5 ** k)
+        got = P.to_scipy(L["rp"], L["ci"], L["val"])
+        assert abs(got - ref).max() < 1e-14
+        assert np.abs(L["v"] - 2.0 ** k).max() < 1e-14
+    # level-0 aggregates are 2x2 blocks with P entries 1/2
+    L0 = H.level(0)
+    y, x = np.divmod(np.arange(4096), 64)
+    assert np.array_equal(L0["agg"], (y // 2) * 32 + x // 2)
+    assert np.abs(L0["p"] - 0.5).max() < 1e-15
+    # sweep 1 = x-pairs, sweep 2 = y-pairs of the 32x64 intermediate grid
+    assert np.array_equal(H.sweep_mate(0, 0), np.arange(4096) ^ 1)
+    yy, xx = np.divmod(np.arange(2048), 32)
+    assert np.array_equal(H.sweep_mate(0, 1), (yy ^ 1) * 32 + xx)
+
+
+def test_hierarchy_poisson3d_closed_form():
+    """m^3 Poisson, v = 1, 3 sweeps: x-, y-, z-pairs -> 2x2x2 cubes, A_c = L_7 / 2,
+    v_c = 2 sqrt 2; the coarse level has the same weights (7/6), so it repeats."""
+    m = 16
+    rp, ci, val = P.poisson3d(m)
+    H = oracle.Hierarchy(rp, ci, val, np.ones(m ** 3), sweeps=3, coarse_max=10)
+    assert [H.level_n(k) for k in range(H.nl)] == [4096, 512, 64, 8]
+    for k in range(1, H.nl):
+        L = H.level(k)
+        mk = m >> k
+        ref = P.to_scipy(*P.poisson3d(mk)) * (0.5 ** k)
+        assert abs(P.to_scipy(L["rp"], L["ci"], L["val"]) - ref).max() < 1e-14
+        assert np.abs(L["v"] - 8.0 ** (k / 2)).max() < 1e-13
+    z, r = np.divmod(np.arange(m ** 3), m * m)
+    y, x = np.divmod(r, m)
+    h = m // 2
+    assert np.array_equal(H.level(0)["agg"], ((z // 2) * h + y // 2) * h + x // 2)
+    assert np.array_equal(H.sweep_mate(0, 0), np.arange(m ** 3) ^ 1)
+
+
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
+def test_hierarchy_composed_prolongator(sweeps):
+    """A^{k+1} = (P_1...P_S)^T A^k (P_1...P_S) up to rounding; P^k orthonormal; P^k v_{k+1} = v_k."""
+    rp, ci, val = P.lognormal_diffusion(12, seed=1)
+    n = len(rp) - 1
+    H = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=sweeps, coarse_max=50)
+    assert H.nl >= 2
+    for k in range(H.nl - 1):
+        F, Cl = H.level(k), H.level(k + 1)
+        Pm = _P_matrix(F["agg"], F["p"], Cl["n"])
+        A = P.to_scipy(F["rp"], F["ci"], F["val"])
+        dense = (Pm.T @ A @ Pm).toarray()
+        got = P.to_scipy(Cl["rp"], Cl["ci"], Cl["val"]).toarray()
+        assert np.abs(got - dense).max() <= 1e-13 * np.abs(dense).max()
+        assert np.abs((Pm.T @ Pm).toarray() - np.eye(Cl["n"])).max() < 1e-14
+        assert np.abs(Pm @ Cl["v"] - F["v"]).max() < 1e-13 * np.abs(F["v"]).max()
+        assert np.bincount(F["agg"]).max() <= 2 ** sweeps
+        assert oracle.check_symmetric(Cl["rp"], Cl["ci"], Cl["val"])
+        # l1 row norms
+        assert np.array_equal(F["dl1"], np.asarray(abs(A).sum(axis=1)).ravel()) or \
+            np.abs(F["dl1"] - np.asarray(abs(A).sum(axis=1)).ravel()).max() < 1e-13 * F["dl1"].max()
+
+
+def test_hierarchy_stops_without_pairs():
+    # diagonal matrix: no edge, so no coarse level is made
+    n = 50
+    rp = np.arange(n + 1, dtype=np.int32)
+    H = oracle.Hierarchy(rp, np.arange(n, dtype=np.int32), np.full(n, 3.0), np.ones(n),
+                         sweeps=2, coarse_max=4)
+    assert H.nl == 1
+
+
+def test_hierarchy_rejects_bad_input():
+    rp = np.array([0, 2, 4], np.int32)
+    with pytest.raises(ValueError):
+        oracle.Hierarchy(rp, np.array([1, 0, 0, 1], np.int32), np.ones(4), np.ones(2), coarse_max=1)
+    with pytest.raises(ValueError):  # zero diagonal
+        oracle.Hierarchy(rp, np.array([0, 1, 0, 1], np.int32), np.array([0.0, -1, -1, 2]),
+                         np.ones(2), coarse_max=1)

@@ -1,0 +1,147 @@
+"""Pins of the oracle's l1-Jacobi smoother (Sec. 3.2), V-cycle (Sec. 2.1, Algorithm 1)
+and flexible CG (Sec. 3.2, Algorithm 3) against textbook identities, scipy's CG and
+direct solves (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+from paper_1810_04221_gb300 import problems as P
+
+
+def _hier(kind="diff", sweeps=2, coarse_max=30, **kw):
+    if kind == "diff":
+        rp, ci, val = P.lognormal_diffusion(8, seed=2)
+    elif kind == "p2":
+        rp, ci, val = P.poisson2d(16)
+    else:
+        rp, ci, val = P.random_spd(400, 5.0, seed=4)
+    n = len(rp) - 1
+    return (rp, ci, val), oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=sweeps,
+                                           coarse_max=coarse_max, **kw)
+
+
+def _dense_levels(H):
+    Ls = [H.level(k) for k in range(H.nl)]
+    A = [P.to_scipy(L["rp"], L["ci"], L["val"]).toarray() for L in Ls]
+    Pm = [sp.csr_matrix((L["p"], (np.arange(L["n"]), L["agg"])),
+                        shape=(L["n"], Ls[k + 1]["n"])).toarray() for k, L in enumerate(Ls[:-1])]
+    D = [L["dl1"] for L in Ls]
+    return A, Pm, D
+
+
+def test_l1_jacobi_norms_and_contraction():
+    (rp, ci, val), H = _hier("rand")
+    A = P.to_scipy(rp, ci, val)
+    L0 = H.level(0)
+    assert np.allclose(L0["dl1"], np.asarray(abs(A).sum(axis=1)).ravel(), rtol=1e-15, atol=0)
+    # l1-Jacobi is convergent for s.p.d. A: the A-norm of the error decreases every sweep
+    n = len(rp) - 1
+    xs = np.random.default_rng(0).standard_normal(n)
+    b = A @ xs
+    x = np.zeros(n)
+    prev = np.sqrt((xs - x) @ (A @ (xs - x)))
+    for _ in range(5):
+        x = H.l1_jacobi(0, b, x, 1)
+        cur = np.sqrt((xs - x) @ (A @ (xs - x)))
+        assert cur < prev
+        prev = cur
+    # textbook identity: error propagation of s sweeps is (I - D^{-1} A)^s
+    Ad = A.toarray()
+    E = np.eye(n) - Ad / L0["dl1"][:, None]
+    x0 = np.random.default_rng(1).standard_normal(n)
+    x3 = H.l1_jacobi(0, b, x0, 3)
+    assert np.abs((xs - x3) - np.linalg.matrix_power(E, 3) @ (xs - x0)).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind,pre,post", [("diff", 1, 1), ("p2", 1, 1), ("rand", 2, 1)])
+def test_vcycle_error_propagation_identity(kind, pre, post):
+    """I - B A = (I - D^-1 A)^post (I - P B_c P^T A) (I - D^-1 A)^pre per level and
+    I - B_c A_c = (I - D_c^-1 A_c)^coarse on the coarsest level (multigrid identity)."""
+    _, H = _hier(kind, pre=pre, post=post, coarse_sweeps=20)
+    A, Pm, D = _dense_levels(H)
+    nl = H.nl
+    assert nl >= 3
+    B = [None] * nl
+    nc = A[-1].shape[0]
+    S = np.eye(nc) - A[-1] / D[-1][:, None]
+    B[-1] = (np.eye(nc) - np.linalg.matrix_power(S, 20)) @ np.linalg.inv(A[-1])
+    for k in range(nl - 2, -1, -1):
+        n = A[k].shape[0]
+        S = np.eye(n) - A[k] / D[k][:, None]
+        C = np.eye(n) - Pm[k] @ B[k + 1] @ Pm[k].T @ A[k]
+        E = np.linalg.matrix_power(S, post) @ C @ np.linalg.matrix_power(S, pre)
+        B[k] = (np.eye(n) - E) @ np.linalg.inv(A[k])
+    n = A[0].shape[0]
+    R = np.random.default_rng(3).standard_normal((n, 4))
+    for c in range(4):
+        w = H.vcycle(R[:, c])
+        ref = B[0] @ R[:, c]
+        assert np.abs(w - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_vcycle_symmetric_positive():
+    _, H = _hier("diff")
+    n = H.level_n(0)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        x, y = rng.standard_normal(n), rng.standard_normal(n)
+        bx, by = H.vcycle(x), H.vcycle(y)
+        assert abs(bx @ y - x @ by) <= 1e-12 * abs(bx @ y) + 1e-14
+        assert x @ bx > 0
+
+
+@pytest.mark.parametrize("prec", [oracle.PREC_IDENTITY, oracle.PREC_L1JACOBI])
+def test_fcg_matches_textbook_pcg(prec):
+    """For a fixed s.p.d. preconditioner, FCG(1) reduces to the classic PCG (scipy.cg)."""
+    (rp, ci, val), H = _hier("rand")
+    A = P.to_scipy(rp, ci, val)
+    n = A.shape[0]
+    xs, b = P.manufactured_rhs(rp, ci, val, seed=1)
+    x, st, it, rr, rt = H.pcg(b, rtol=1e-10, itmax=2000, prec=prec)
+    assert st == oracle.OK
+    count = [0]
+    M = None
+    if prec == oracle.PREC_L1JACOBI:
+        d = H.level(0)["dl1"]
+        M = spla.LinearOperator((n, n), matvec=lambda r: r / d)
+    xref, info = spla.cg(A, b, rtol=1e-10, atol=0.0, maxiter=2000, M=M,
+                         callback=lambda _: count.__setitem__(0, count[0] + 1))
+    assert info == 0
+    assert abs(it - count[0]) <= 1
+    assert np.abs(x - xref).max() <= 1e-7 * np.abs(xref).max()
+
+
+@pytest.mark.parametrize("kind", ["diff", "p2", "rand"])
+def test_fcg_amg_solution_vs_direct(kind):
+    (rp, ci, val), H = _hier(kind)
+    A = P.to_scipy(rp, ci, val)
+    xs, b = P.manufactured_rhs(rp, ci, val, seed=2)
+    x, st, it, rr, rt = H.pcg(b, rtol=1e-10, itmax=500)
+    assert st == oracle.OK and rr <= 1e-10
+    assert rt <= 1e-9
+    xd = spla.spsolve(A.tocsc(), b)
+    assert np.abs(x - xd).max() <= 1e-7 * np.abs(xd).max()
+
+
+def test_fcg_zero_rhs_and_itmax():
+    _, H = _hier("p2")
+    n = H.level_n(0)
+    x, st, it, rr, rt = H.pcg(np.zeros(n))
+    assert st == oracle.OK and it == 0 and np.all(x == 0)
+    b = np.random.default_rng(0).standard_normal(n)
+    x, st, it, rr, rt = H.pcg(b, rtol=1e-30, itmax=3)
+    assert st == oracle.ERR_NOT_CONVERGED and it == 3
+
+
+def test_fcg_poisson64_reference_iterations():
+    """64^2 Poisson, 2 sweeps, coarse <= 40, rtol 1e-8: converges; the recursive and the
+    true residual agree."""
+    rp, ci, val = P.poisson2d(64)
+    H = oracle.Hierarchy(rp, ci, val, np.ones(4096), sweeps=2, coarse_max=40)
+    xs, b = P.manufactured_rhs(rp, ci, val, seed=0)
+    x, st, it, rr, rt = H.pcg(b, rtol=1e-8)
+    assert st == oracle.OK and 5 < it < 60
+    assert abs(rr - rt) < 1e-10
+    assert np.abs(x - xs).max() < 1e-5
