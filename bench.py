@@ -1,0 +1,411 @@
+"""Benchmark: AMG setup + FCG solve to 1e-8 relative residual on one GB300 per rank.
+
+A step is one pass of the whole hot path over the workload: amg_setup (weights, Suitor
+matching, aggregation, prolongator, Galerkin products, level after level) followed by
+amg_pcg_solve (FCG with the l1-Jacobi V-cycle) from x = 0, then amg_free.
+
+Default workload: 3D Poisson, 7-point stencil on 128^3 (n = 2,097,152, nnz = 14,581,760),
+FP64 CSR, v = 1, 3 matching sweeps per level (aggregates of 8), coarse n <= 1000,
+b = A x* with x* ~ U[-1, 1] (seed 0), FP64 setup + FP64 FCG / V-cycle, rtol 1e-8.
+
+Prints ONE JSON line (rank 0).  `value` is milliseconds per step (setup + solve) with the
+inputs already resident in HBM; `e2e` times the same C-ABI calls with host buffers
+(pinned host -> device copies of the CSR, v and b, and the device -> host copy of x inside
+the timed region).  `--impl reference` times the CPU FP64 oracle (the reference arm).
+Under torchrun every rank runs an independent replica (the solver does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1810_04221_gb300 import problems as P  # noqa: E402
+
+METRIC = "AMG setup ms + PCG solve ms to 1e-8 rel. residual"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(name: str):
+    """(description dict, (rp, ci, val), v, b, x*, sweeps, coarse_max, fp32)."""
+    if name == "poisson3d_128":
+        mat = P.poisson3d(128)
+        n = len(mat[0]) - 1
+        v = np.ones(n)
+        sweeps, cmax, fp32 = 3, 1000, False
+        desc = "3D Poisson 7-point 128^3, v=1, 3 sweeps/level, coarse<=1000, FP64 setup+FCG/V-cycle"
+    elif name == "poisson2d_64":
+        mat = P.poisson2d(64)
+        n = len(mat[0]) - 1
+        v = np.ones(n)
+        sweeps, cmax, fp32 = 2, 40, False
+        desc = "2D Poisson 5-point 64^2, v=1, 2 sweeps/level, coarse<=40, FP64"
+    elif name == "lognormal_160":
+        mat = P.lognormal_diffusion(160, sigma=2.0, seed=0)
+        n = len(mat[0]) - 1
+        v = np.ones(n)
+        sweeps, cmax, fp32 = 3, 1000, True
+        desc = "3D FV diffusion 160^3, log-kappa N(0,4), 3 sweeps/level, coarse<=1000, FP32 V-cycle in FP64 FCG"
+    elif name == "elasticity_64":
+        mat = P.elasticity_q1(64)
+        n = len(mat[0]) - 1
+        v = P.smooth_vector_components(n, seed=0)
+        sweeps, cmax, fp32 = 2, 1000, True
+        desc = "3D Q1 elasticity 64^3 nodes, x=0 clamped, 2 sweeps/level, coarse<=1000, FP32 V-cycle in FP64 FCG"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    xs, b = P.manufactured_rhs(*mat, seed=0)
+    return desc, mat, v, b, xs, sweeps, cmax, fp32
+
+
+# --------------------------------------------------------------------- helpers ----
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic_for(kernel_class: str):
+    """DRAM bytes per launch from a committed ncu summary, or None if absent or stale."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        e = d[kernel_class]
+        src = os.path.join(ROOT, e["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if sha != e["source_sha256"]:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:  # noqa: BLE001
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:  # noqa: BLE001
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- CUDA arm ----
+
+def run_cuda(args, rank, world, dist):
+    import torch
+    from paper_1810_04221_gb300 import binding as B
+    from paper_1810_04221_gb300 import build as cuda_build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    if dist is not None:
+        dist.barrier()
+    B.load()
+    desc, mat, v, b, xs, sweeps, cmax, fp32 = workload(args.workload)
+    if args.fp32 is not None:
+        fp32 = bool(args.fp32)
+    rp, ci, val = mat
+    n, nnz = len(rp) - 1, len(ci)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    d_rp, d_ci, d_val, d_v, d_b = dev(rp), dev(ci), dev(val), dev(v), dev(b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def params(trace=0, filt=""):
+        return B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, vcycle_fp32=int(fp32), trace=trace,
+                                    trace_filter=filt, check_input=0)
+
+    def step(prm, evs=None):
+        if evs:
+            evs[0].record(stream)
+        h = B.amg_setup(d_rp, d_ci, d_val, d_v, prm)
+        if evs:
+            evs[1].record(stream)
+        x.zero_()
+        st, info = B.amg_pcg_solve(h, d_b, x, rtol=args.rtol, itmax=args.itmax)
+        if evs:
+            evs[2].record(stream)
+        return h, st, info
+
+    # warm-up; the first one traces every kernel class to find the dominant one
+    dominant, trace_all = None, []
+    for w in range(max(args.warmup, 1)):
+        h, st, info = step(params(trace=1 if w == 0 else 0))
+        if w == 0:
+            trace_all = B.amg_trace(h)
+            if trace_all:
+                dominant = max(trace_all, key=lambda e: e["total_ms"])["name"]
+        h.free()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, device events on the launching stream, dominant class traced
+    clocks = Clocks(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    traces, infos, statuses = [], [], []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = B.amg_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        h, st, info = step(params(trace=1, filt=dominant or ""), evs[k])
+        traces.append(B.amg_trace(h))
+        infos.append(info)
+        statuses.append(st)
+        h.free()
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = B.amg_launch_count() - l0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    setup_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    solve_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
+
+    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    h_rp, h_ci, h_val, h_v, h_b = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (rp, ci, val, v, b))
+    h_x = torch.empty(n, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_ci, h_val, h_v, h_b))
+    d2h = h_x.numel() * h_x.element_size()
+
+    def e2e_step():
+        g = [t.cuda(non_blocking=True) for t in (h_rp, h_ci, h_val, h_v, h_b)]
+        hh = B.amg_setup(g[0], g[1], g[2], g[3], params())
+        xx = torch.zeros(n, dtype=torch.float64, device="cuda")
+        B.amg_pcg_solve(hh, g[4], xx, rtol=args.rtol, itmax=args.itmax)
+        h_x.copy_(xx, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        hh.free()
+
+    e2e_step()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    # roofline of the dominant kernel class over the timed region
+    peak, peak_kind = _peaks()
+    roof = None
+    if dominant:
+        ms = sum(e["total_ms"] for t in traces for e in t if e["name"] == dominant)
+        byt = sum(e["bytes"] for t in traces for e in t if e["name"] == dominant)
+        nl = sum(e["launches"] for t in traces for e in t if e["name"] == dominant)
+        if ms > 0 and nl > 0:
+            ach = byt / (ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": dominant, "achieved": round(ach, 1), "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": round(ach / peak, 4),
+                    "traffic": _traffic_for(dominant), "launches": nl,
+                    "bytes_per_launch": byt / nl, "avg_launch_us": ms / nl * 1e3}
+
+    # FP32 V-cycle variant on the same workload (not part of the timed value)
+    variant = None
+    if args.variant and dist is None:
+        prm32 = B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, vcycle_fp32=int(not fp32),
+                                     check_input=0)
+        res = []
+        for _ in range(3):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            h, st, info = step(prm32, e)
+            h.free()
+            torch.cuda.synchronize()
+            res.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), info))
+        best = min(res, key=lambda r: r[0] + r[1])
+        variant = {"vcycle": "fp32" if not fp32 else "fp64", "ms_per_step": round(best[0] + best[1], 3),
+                   "setup_ms": round(best[0], 3), "solve_ms": round(best[1], 3), "iters": best[2]["iters"],
+                   "rel_res_true": best[2]["rel_res_true"],
+                   "err_vs_xstar": float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))}
+
+    # CPU baseline: the oracle as it stands, one full step, rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mat, v, b, sweeps, cmax, args.rtol, args.itmax)
+
+    last = infos[-1]
+    out = {
+        "metric": METRIC, "value": round(ms_per_step, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not fp32 else "f64+f32-vcycle",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "n": n, "nnz": nnz, "sweeps_per_level": sweeps,
+                   "coarse_max": cmax, "rtol": args.rtol, "vcycle_fp32": bool(fp32),
+                   "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB), no flush" % ((12 * nnz + 4 * n) / 1e6),
+                   "parallelism": f"replicas{world}"},
+        "setup_ms": round(statistics.median(setup_ms), 3), "solve_ms": round(statistics.median(solve_ms), 3),
+        "iters": last["iters"], "ms_per_iter": round(statistics.median(solve_ms) / max(last["iters"], 1), 4),
+        "levels": last["nl"], "vcmplx": round(last["vcmplx"], 4), "cratio": round(last["cratio"], 4),
+        "rel_res_true": last["rel_res_true"], "err_vs_xstar": err,
+        "status": [B.status_name(s) for s in statuses][-1],
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "kernel_classes": sorted([{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
+                                  for e in trace_all], key=lambda e: -e["total_ms"])[:12],
+    }
+    if variant:
+        out["variant"] = variant
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline(mat, v, b, sweeps, cmax, rtol, itmax):
+    import oracle
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax)
+    t1 = time.perf_counter()
+    _, st, it, _, _ = H.pcg(b, rtol=rtol, itmax=itmax)
+    t2 = time.perf_counter()
+    H.close()
+    return {"value": round((t2 - t0) * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "setup_ms": round((t1 - t0) * 1e3, 1), "solve_ms": round((t2 - t1) * 1e3, 1), "iters": it,
+            "sample": "the full workload, one step (setup + FCG), single-threaded C oracle",
+            "host_cores": os.cpu_count()}
+
+
+# --------------------------------------------------------------------- reference arm ----
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    desc, mat, v, b, xs, sweeps, cmax, fp32 = workload(args.workload)
+    # warm-up on a small instance of the same problem family (pages code in)
+    small = P.poisson3d(16)
+    for _ in range(args.warmup):
+        Hs = oracle.Hierarchy(*small, np.ones(16 ** 3), sweeps=sweeps, coarse_max=cmax)
+        Hs.pcg(P.manufactured_rhs(*small, seed=0)[1], rtol=args.rtol)
+        Hs.close()
+    times, it = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax)
+        _, st, it, _, _ = H.pcg(b, rtol=args.rtol, itmax=args.itmax)
+        times.append((time.perf_counter() - t0) * 1e3)
+        H.close()
+    ms = sum(times) / len(times)
+    sample = "the full workload per step (setup + FCG), single-threaded C oracle; warm-up on 16^3"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "n": len(mat[0]) - 1, "nnz": len(mat[1])},
+        "iters": it,
+        "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--workload", default="poisson3d_128",
+                    choices=["poisson3d_128", "poisson2d_64", "lognormal_160", "elasticity_64"])
+    ap.add_argument("--fp32", type=int, default=None, help="override the workload's V-cycle precision")
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--itmax", type=int, default=5000)
+    ap.add_argument("--variant", type=int, default=1, help="also time the other V-cycle precision")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "cuda" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_cuda(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

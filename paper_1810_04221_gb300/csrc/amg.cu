@@ -1,0 +1,826 @@
+// amg.cu -- the hierarchy driver (Sec. 2.1 setup, Sec. 5 parameters), the V-cycle
+// (Sec. 2.1, Algorithm 1), the flexible CG (Sec. 3.2, Algorithm 3) and the C ABI.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "coarsen.cuh"
+#include "solve.cuh"
+#include "trace.cuh"
+
+namespace cwm {
+const char *last_error();
+}
+
+using namespace cwm;
+
+namespace {
+
+struct Level {
+  int n = 0;
+  long long nnz = 0;
+  int tile = 8;
+  DBuf<int> rp, ci;
+  DBuf<double> val, v, diag, dl1, dinv;
+  DBuf<float> val32, dinv32;
+  // transfer to level k+1 (empty on the coarsest level)
+  DBuf<int> agg, mptr, mlist;
+  DBuf<double> p;
+  DBuf<float> p32;
+  int nsweeps = 0;
+  std::vector<int> sweep_n;
+  std::vector<DBuf<int>> sweep_mate;
+  // V-cycle work vectors
+  DBuf<double> b, x, t1, t2;
+  DBuf<float> b32, x32, t132, t232;
+
+  CsrView<double> view64() const {
+    CsrView<double> a;
+    a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val.get(); a.tile = tile;
+    return a;
+  }
+  CsrView<float> view32() const {
+    CsrView<float> a;
+    a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get(); a.tile = tile;
+    return a;
+  }
+};
+
+// One matching sweep's products (owned until moved into a level).
+struct SweepOut {
+  int n = 0;
+  long long nnz = 0;
+  DBuf<int> rp, ci, agg;
+  DBuf<double> val, diag, dl1, v, p;
+};
+
+// Pinned host mailbox for the few device -> host reads.
+struct Mailbox {
+  int *ints = nullptr;        // 16
+  double *dbls = nullptr;     // 16
+  amg_status init() {
+    if (!ints) CWM_CUDA(cudaMallocHost((void **)&ints, 16 * sizeof(int)));
+    if (!dbls) CWM_CUDA(cudaMallocHost((void **)&dbls, 16 * sizeof(double)));
+    return AMG_OK;
+  }
+  ~Mailbox() {
+    if (ints) cudaFreeHost(ints);
+    if (dbls) cudaFreeHost(dbls);
+  }
+};
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct amg_hierarchy {
+  amg_params prm{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<Level> lev;
+  DBuf<int> err;
+  Mailbox box;
+  // FCG vectors and reductions
+  DBuf<double> r, w, d, vv, q, part, part2, scal;
+  double t_setup_ms = 0.0, t_solve_ms = 0.0;
+  Tracer trace;
+};
+
+namespace {
+
+// Installs h's tracer for the calling thread for the lifetime of the guard.
+struct TraceGuard {
+  Tracer *prev;
+  int prev_level;
+  explicit TraceGuard(amg_hierarchy *h) : prev(g_tracer), prev_level(g_trace_level) {
+    g_tracer = h->trace.on ? &h->trace : nullptr;
+    g_trace_level = -1;
+  }
+  ~TraceGuard() {
+    g_tracer = prev;
+    g_trace_level = prev_level;
+  }
+};
+
+struct LevelTag {
+  int prev;
+  explicit LevelTag(int k) : prev(g_trace_level) { g_trace_level = k; }
+  ~LevelTag() { g_trace_level = prev; }
+};
+
+amg_status read_err(amg_hierarchy *h, const char *where) {
+  CWM_CUDA(cudaMemcpyAsync(h->box.ints + 8, h->err.get(), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CWM_CUDA(cudaStreamSynchronize(h->stream));
+  int bits = h->box.ints[8];
+  if (bits) {
+    CWM_CUDA(cudaMemsetAsync(h->err.get(), 0, sizeof(int), h->stream));
+    return status_from_device_bits(bits, where);
+  }
+  return AMG_OK;
+}
+
+long long default_cap(const amg_params &prm, long long n, long long nnz) {
+  return prm.loop_cap > 0 ? prm.loop_cap : nnz + n + 1024;
+}
+
+// Builds level k+1 from level k by up to S sweeps; *made = false when no pair formed.
+amg_status coarsen_level(amg_hierarchy *h, bool *made) {
+  cudaStream_t s = h->stream;
+  Level &F = h->lev.back();
+  const int S = h->prm.sweeps_per_level;
+  *made = false;
+  LevelTag tag((int)h->lev.size() - 1);
+
+  // scratch sized for the largest (first) sweep
+  const int nf = F.n;
+  const long long nnzf = F.nnz;
+  DBuf<double> w;
+  DBuf<unsigned char> skeys;
+  DBuf<int> mate, m1, m2, ids, scan, cnt, longr, misc;
+  CWM_TRY(w.alloc(nnzf, s));
+  CWM_TRY(skeys.alloc(suitor_scratch_bytes(nf), s));
+  CWM_TRY(mate.alloc(nf, s));
+  CWM_TRY(m1.alloc(nf, s));
+  CWM_TRY(m2.alloc(nf, s));
+  CWM_TRY(ids.alloc((size_t)nf + 1, s));
+  CWM_TRY(scan.alloc(scan_scratch_ints(nf), s));
+  CWM_TRY(cnt.alloc((size_t)nf + 1, s));
+  CWM_TRY(longr.alloc(nf, s));
+  CWM_TRY(misc.alloc(4, s));
+
+  std::vector<SweepOut> sw;
+  sw.reserve(S);
+  // the operator matched by the current sweep
+  int cn = F.n;
+  long long cnnz = F.nnz;
+  const int *crp = F.rp.get(), *cci = F.ci.get();
+  const double *cval = F.val.get(), *cdiag = F.diag.get(), *cv = F.v.get();
+  F.sweep_n.clear();
+  F.sweep_mate.clear();
+
+  for (int sweep = 0; sweep < S; ++sweep) {
+    CWM_TRY(edge_weights(cn, cnnz, crp, cci, cval, cdiag, cv, w.get(), s));
+    CWM_TRY(suitor_match(cn, cnnz, crp, cci, w.get(), skeys.get(), mate.get(),
+                         default_cap(h->prm, cn, cnnz), h->err.get(), s));
+    SweepOut o;
+    CWM_TRY(o.agg.alloc(cn, s));
+    CWM_TRY(o.p.alloc(cn, s));
+    CWM_TRY(o.v.alloc(cn, s));
+    CWM_TRY(aggregate(cn, mate.get(), cv, o.agg.get(), o.p.get(), o.v.get(), m1.get(), m2.get(), ids.get(),
+                      scan.get(), misc.get(), s));
+    CWM_CUDA(cudaMemcpyAsync(h->box.ints, misc.get(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CWM_TRY(read_err(h, "amg_setup (matching)"));  // synchronises
+    const int nc = h->box.ints[0], npairs = h->box.ints[1];
+    if (h->prm.keep_sweeps) {
+      DBuf<int> keep;
+      CWM_TRY(keep.alloc(cn, s));
+      CWM_CUDA(cudaMemcpyAsync(keep.get(), mate.get(), sizeof(int) * (size_t)cn, cudaMemcpyDeviceToDevice, s));
+      F.sweep_mate.push_back(std::move(keep));
+      F.sweep_n.push_back(cn);
+    }
+    if (npairs == 0) break;
+    // Galerkin product into arrays of capacity cnnz (nnz(A_c) <= nnz(A) always)
+    o.n = nc;
+    CWM_TRY(o.rp.alloc((size_t)nc + 1, s));
+    CWM_TRY(o.ci.alloc(cnnz, s));
+    CWM_TRY(o.val.alloc(cnnz, s));
+    CWM_TRY(o.diag.alloc(nc, s));
+    CWM_TRY(o.dl1.alloc(nc, s));
+    GalerkinWork gw;
+    gw.cnt = cnt.get();
+    gw.long_rows = longr.get();
+    gw.n_long = misc.get() + 2;
+    gw.scan = scan.get();
+    gw.n_fine = cn;
+    gw.nnz_fine = cnnz;
+    CWM_TRY(galerkin_count(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(), gw,
+                           h->err.get(), s));
+    CWM_TRY(galerkin_fill(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(),
+                          o.ci.get(), o.val.get(), o.diag.get(), o.dl1.get(), gw, h->err.get(), s));
+    CWM_CUDA(cudaMemcpyAsync(h->box.ints + 4, o.rp.get() + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CWM_TRY(read_err(h, "amg_setup (Galerkin)"));
+    o.nnz = h->box.ints[4];
+    sw.push_back(std::move(o));
+    SweepOut &last = sw.back();
+    cn = last.n;
+    cnnz = last.nnz;
+    crp = last.rp.get();
+    cci = last.ci.get();
+    cval = last.val.get();
+    cdiag = last.diag.get();
+    cv = last.v.get();
+  }
+  F.nsweeps = (int)sw.size();
+  if (sw.empty()) return AMG_OK;
+
+  // composed prolongator of level k, and its transpose as member lists
+  SweepMaps maps{};
+  maps.count = (int)sw.size();
+  for (int i = 0; i < maps.count; ++i) {
+    maps.agg[i] = sw[i].agg.get();
+    maps.p[i] = sw[i].p.get();
+  }
+  const int nc = sw.back().n;
+  CWM_TRY(F.agg.alloc(F.n, s));
+  CWM_TRY(F.p.alloc(F.n, s));
+  CWM_TRY(compose(F.n, maps, F.agg.get(), F.p.get(), s));
+  CWM_TRY(F.mptr.alloc((size_t)nc + 1, s));
+  CWM_TRY(F.mlist.alloc(F.n, s));
+  CWM_TRY(member_lists(F.n, nc, F.agg.get(), F.mptr.get(), F.mlist.get(), cnt.get(), scan.get(), s));
+
+  // the new level takes the last sweep's operator
+  SweepOut &last = sw.back();
+  Level C;
+  C.n = last.n;
+  C.nnz = last.nnz;
+  C.tile = tile_for_mean(C.n ? (double)C.nnz / C.n : 1.0);
+  C.rp = std::move(last.rp);
+  C.ci = std::move(last.ci);
+  C.val = std::move(last.val);
+  C.v = std::move(last.v);
+  C.diag = std::move(last.diag);
+  C.dl1 = std::move(last.dl1);
+  h->lev.push_back(std::move(C));
+  *made = (int)sw.size() == S;  // a sweep without pairs ends the hierarchy after this level
+  return AMG_OK;
+}
+
+amg_status finish_level(amg_hierarchy *h, Level &L) {
+  cudaStream_t s = h->stream;
+  CWM_TRY(L.dinv.alloc(L.n, s));
+  const bool f32 = h->prm.vcycle_fp32 != 0;
+  if (f32) CWM_TRY(L.dinv32.alloc(L.n, s));
+  CWM_TRY(reciprocal(L.n, L.dl1.get(), L.dinv.get(), f32 ? L.dinv32.get() : nullptr, s));
+  CWM_TRY(L.b.alloc(L.n, s));
+  CWM_TRY(L.x.alloc(L.n, s));
+  CWM_TRY(L.t1.alloc(L.n, s));
+  CWM_TRY(L.t2.alloc(L.n, s));
+  if (f32) {
+    CWM_TRY(L.val32.alloc(L.nnz, s));
+    CWM_TRY(to_float(L.nnz, L.val.get(), L.val32.get(), s));
+    CWM_TRY(L.b32.alloc(L.n, s));
+    CWM_TRY(L.x32.alloc(L.n, s));
+    CWM_TRY(L.t132.alloc(L.n, s));
+    CWM_TRY(L.t232.alloc(L.n, s));
+    if (L.p.get()) {
+      CWM_TRY(L.p32.alloc(L.n, s));
+      CWM_TRY(to_float(L.n, L.p.get(), L.p32.get(), s));
+    }
+  }
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ V-cycle ----
+template <class V>
+struct LevelVec;
+template <>
+struct LevelVec<double> {
+  static CsrView<double> A(const Level &L) { return L.view64(); }
+  static const double *dinv(const Level &L) { return L.dinv.get(); }
+  static const double *p(const Level &L) { return L.p.get(); }
+  static double *b(Level &L) { return L.b.get(); }
+  static double *x(Level &L) { return L.x.get(); }
+  static double *t1(Level &L) { return L.t1.get(); }
+  static double *t2(Level &L) { return L.t2.get(); }
+};
+template <>
+struct LevelVec<float> {
+  static CsrView<float> A(const Level &L) { return L.view32(); }
+  static const float *dinv(const Level &L) { return L.dinv32.get(); }
+  static const float *p(const Level &L) { return L.p32.get(); }
+  static float *b(Level &L) { return L.b32.get(); }
+  static float *x(Level &L) { return L.x32.get(); }
+  static float *t1(Level &L) { return L.t132.get(); }
+  static float *t2(Level &L) { return L.t232.get(); }
+};
+
+// x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
+template <class V>
+amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
+  using LV = LevelVec<V>;
+  cudaStream_t s = h->stream;
+  Level &L = h->lev[k];
+  LevelTag tag(k);
+  const CsrView<V> A = LV::A(L);
+  const V *dinv = LV::dinv(L);
+  V *t1 = LV::t1(L), *t2 = LV::t2(L);
+  const int nl = (int)h->lev.size();
+  if (k == nl - 1) {  // coarsest: l1-Jacobi sweeps from zero
+    const int sweeps = h->prm.coarse_sweeps;
+    if (A.n <= kCoarseBlockMax) return coarse_solve_block<V>(A, dinv, b, x, sweeps, s);
+    if (sweeps <= 0) { CWM_CUDA(cudaMemsetAsync(x, 0, sizeof(V) * (size_t)A.n, s)); return AMG_OK; }
+    const V *cur = nullptr;
+    for (int i = 0; i < sweeps; ++i) {
+      V *dst = i == sweeps - 1 ? x : (cur == t1 ? t2 : t1);
+      if (i == 0) CWM_TRY(scale<V>(A.n, dinv, b, dst, s));
+      else CWM_TRY(jacobi<V>(A, dinv, b, cur, dst, s));
+      cur = dst;
+    }
+    return AMG_OK;
+  }
+  // pre-smoothing from zero: the first sweep is x = D^{-1} b
+  const V *xs = nullptr;
+  for (int i = 0; i < h->prm.pre_sweeps; ++i) {
+    V *dst = (xs == t1) ? t2 : t1;
+    if (i == 0) CWM_TRY(scale<V>(A.n, dinv, b, dst, s));
+    else CWM_TRY(jacobi<V>(A, dinv, b, xs, dst, s));
+    xs = dst;
+  }
+  Level &C = h->lev[k + 1];
+  CWM_TRY(resid_restrict<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, LV::b(C), s));
+  CWM_TRY(vcycle_level<V>(h, k + 1, LV::b(C), LV::x(C)));
+  V *y = (xs == t1) ? t2 : t1;
+  CWM_TRY(prolong<V>(A.n, L.agg.get(), LV::p(L), LV::x(C), xs, y, s));
+  const int post = h->prm.post_sweeps;
+  if (post <= 0) {
+    CWM_CUDA(cudaMemcpyAsync(x, y, sizeof(V) * (size_t)A.n, cudaMemcpyDeviceToDevice, s));
+    return AMG_OK;
+  }
+  const V *cur = y;
+  for (int i = 0; i < post; ++i) {
+    V *dst = i == post - 1 ? x : (cur == t1 ? t2 : t1);
+    CWM_TRY(jacobi<V>(A, dinv, b, cur, dst, s));
+    cur = dst;
+  }
+  return AMG_OK;
+}
+
+amg_status apply_vcycle(amg_hierarchy *h, const double *r, double *w) {
+  if (!h->prm.vcycle_fp32) return vcycle_level<double>(h, 0, r, w);
+  Level &L0 = h->lev[0];
+  CWM_TRY(to_float(L0.n, r, L0.b32.get(), h->stream));
+  CWM_TRY(vcycle_level<float>(h, 0, L0.b32.get(), L0.x32.get()));
+  return to_double(L0.n, L0.x32.get(), w, h->stream);
+}
+
+amg_status validate_handle(amg_handle h) {
+  if (!h) {
+    set_error("NULL handle");
+    return AMG_ERR_INVALID_ARG;
+  }
+  return AMG_OK;
+}
+
+}  // namespace
+
+// ============================================================ C ABI ====
+extern "C" {
+
+void amg_default_params(amg_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->sweeps_per_level = 2;
+  p->coarse_max = 40;
+  p->max_levels = 40;
+  p->pre_sweeps = 1;
+  p->post_sweeps = 1;
+  p->coarse_sweeps = 20;
+  p->vcycle_fp32 = 0;
+  p->check_input = 1;
+  p->keep_sweeps = 0;
+  p->loop_cap = 0;
+  p->trace = 0;
+}
+
+const char *amg_status_string(amg_status s) {
+  switch (s) {
+    case AMG_OK: return "AMG_OK";
+    case AMG_ERR_INVALID_ARG: return "AMG_ERR_INVALID_ARG";
+    case AMG_ERR_NOT_SPD: return "AMG_ERR_NOT_SPD";
+    case AMG_ERR_CUDA: return "AMG_ERR_CUDA";
+    case AMG_ERR_OOM: return "AMG_ERR_OOM";
+    case AMG_ERR_TIMEOUT: return "AMG_ERR_TIMEOUT";
+    case AMG_ERR_BREAKDOWN: return "AMG_ERR_BREAKDOWN";
+    case AMG_ERR_NOT_CONVERGED: return "AMG_ERR_NOT_CONVERGED";
+    case AMG_ERR_UNSUPPORTED: return "AMG_ERR_UNSUPPORTED";
+  }
+  return "AMG_ERR_UNKNOWN";
+}
+
+const char *amg_last_error(void) { return cwm::last_error(); }
+
+static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_t *ci, const double *val,
+                             const double *v, const amg_params *params, void *stream, amg_hierarchy *h) {
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  CWM_CUDA(cudaGetDevice(&h->device));
+  if (params) h->prm = *params;
+  else amg_default_params(&h->prm);
+  amg_params &P = h->prm;
+  h->trace.on = P.trace != 0;
+  P.trace_filter[sizeof(P.trace_filter) - 1] = '\0';
+  h->trace.filter = P.trace_filter;
+  TraceGuard tg(h);
+  if (P.sweeps_per_level < 1 || P.sweeps_per_level > kMaxSweeps || P.max_levels < 1 || P.pre_sweeps < 0 ||
+      P.post_sweeps < 0 || P.coarse_sweeps < 0 || P.coarse_max < 0) {
+    set_error("amg_setup: parameter out of range");
+    return AMG_ERR_INVALID_ARG;
+  }
+  retain_pool_memory();
+  CWM_TRY(h->box.init());
+  CWM_TRY(h->err.alloc(1, s));
+  CWM_CUDA(cudaMemsetAsync(h->err.get(), 0, sizeof(int), s));
+
+  h->lev.emplace_back();
+  Level &L0 = h->lev[0];
+  L0.n = n;
+  L0.nnz = nnz;
+  L0.tile = tile_for_mean((double)nnz / n);
+  CWM_TRY(L0.rp.alloc((size_t)n + 1, s));
+  CWM_TRY(L0.ci.alloc(nnz, s));
+  CWM_TRY(L0.val.alloc(nnz, s));
+  CWM_TRY(L0.v.alloc(n, s));
+  CWM_TRY(L0.diag.alloc(n, s));
+  CWM_TRY(L0.dl1.alloc(n, s));
+  CWM_CUDA(cudaMemcpyAsync(L0.rp.get(), rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+  if (nnz) {
+    CWM_CUDA(cudaMemcpyAsync(L0.ci.get(), ci, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
+    CWM_CUDA(cudaMemcpyAsync(L0.val.get(), val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
+  }
+  CWM_CUDA(cudaMemcpyAsync(L0.v.get(), v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  if (P.check_input) {
+    CWM_TRY(check_input(n, nnz, L0.rp.get(), L0.ci.get(), L0.val.get(), true, h->err.get(), s));
+    CWM_TRY(read_err(h, "amg_setup (input check)"));
+  }
+  CWM_TRY(extract_diag(n, L0.rp.get(), L0.ci.get(), L0.val.get(), L0.diag.get(), h->err.get(), s));
+  CWM_TRY(l1_norms(L0.view64(), L0.dl1.get(), s));
+  CWM_TRY(read_err(h, "amg_setup (diagonal)"));
+
+  while ((int)h->lev.size() < P.max_levels && h->lev.back().n > P.coarse_max) {
+    bool made = false;
+    const size_t before = h->lev.size();
+    CWM_TRY(coarsen_level(h, &made));
+    if (h->lev.size() == before) break;  // no pair at all: the current level is the coarsest
+    if (!made) break;
+  }
+  for (Level &L : h->lev) CWM_TRY(finish_level(h, L));
+  h->lev.back().nsweeps = 0;
+
+  // FCG work vectors
+  CWM_TRY(h->r.alloc(n, s));
+  CWM_TRY(h->w.alloc(n, s));
+  CWM_TRY(h->d.alloc(n, s));
+  CWM_TRY(h->vv.alloc(n, s));
+  CWM_TRY(h->q.alloc(n, s));
+  const int nb = fcg_partial_blocks(n);
+  CWM_TRY(h->part.alloc(3 * (size_t)nb, s));
+  CWM_TRY(h->part2.alloc(nb, s));
+  CWM_TRY(h->scal.alloc(kFcgSlots, s));
+  CWM_CUDA(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+                     const double *d_v, const amg_params *params, void *stream, amg_handle *out) {
+  if (!out) {
+    set_error("amg_setup: out is NULL");
+    return AMG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (n < 1 || nnz < 0 || nnz >= (int64_t)INT32_MAX || !d_row_ptr || !d_v || (nnz > 0 && (!d_col || !d_val))) {
+    set_error("amg_setup: invalid size or NULL pointer (n=%d, nnz=%lld)", n, (long long)nnz);
+    return AMG_ERR_INVALID_ARG;
+  }
+  const double t0 = now_ms();
+  amg_hierarchy *h = new (std::nothrow) amg_hierarchy();
+  if (!h) return AMG_ERR_OOM;
+  amg_status st = setup_impl(n, nnz, d_row_ptr, d_col, d_val, d_v, params, stream, h);
+  if (st != AMG_OK) {
+    cudaDeviceSynchronize();
+    (void)cudaGetLastError();
+    g_sync_free = true;
+    delete h;
+    g_sync_free = false;
+    return st;
+  }
+  h->t_setup_ms = now_ms() - t0;
+  *out = h;
+  return AMG_OK;
+}
+
+void amg_free(amg_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  g_sync_free = true;
+  delete h;
+  g_sync_free = false;
+  (void)cudaGetLastError();
+}
+
+int amg_num_levels(amg_handle h) { return h ? (int)h->lev.size() : -1; }
+
+amg_status amg_level_info(amg_handle h, int level, int *n, int64_t *nnz, int *nsweeps) {
+  CWM_TRY(validate_handle(h));
+  if (level < 0 || level >= (int)h->lev.size()) {
+    set_error("amg_level_info: level %d out of range", level);
+    return AMG_ERR_INVALID_ARG;
+  }
+  const Level &L = h->lev[level];
+  if (n) *n = L.n;
+  if (nnz) *nnz = L.nnz;
+  if (nsweeps) *nsweeps = L.nsweeps;
+  return AMG_OK;
+}
+
+amg_status amg_stats(amg_handle h, amg_info *info) {
+  CWM_TRY(validate_handle(h));
+  if (!info) return AMG_ERR_INVALID_ARG;
+  const int nl = (int)h->lev.size();
+  double z = 0.0, c = 0.0;
+  for (int k = 0; k < nl; ++k) z += (double)h->lev[k].nnz;
+  for (int k = 1; k < nl; ++k) c += (double)h->lev[k - 1].n / (double)h->lev[k].n;
+  info->nl = nl;
+  info->vcmplx = h->lev[0].nnz ? z / (double)h->lev[0].nnz : 0.0;
+  info->cratio = c / nl;
+  info->t_setup_ms = h->t_setup_ms;
+  info->t_solve_ms = h->t_solve_ms;
+  return AMG_OK;
+}
+
+amg_status amg_level_export(amg_handle h, int level, int32_t *d_row_ptr, int32_t *d_col, double *d_val,
+                            double *d_v, double *d_dl1, int32_t *d_agg, double *d_p, void *stream) {
+  CWM_TRY(validate_handle(h));
+  if (level < 0 || level >= (int)h->lev.size()) {
+    set_error("amg_level_export: level %d out of range", level);
+    return AMG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CWM_CUDA(cudaStreamSynchronize(h->stream));
+  const Level &L = h->lev[level];
+  const size_t n = L.n, z = L.nnz;
+  auto cp = [&](void *dst, const void *src, size_t bytes) -> amg_status {
+    if (dst && src && bytes) CWM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    return AMG_OK;
+  };
+  CWM_TRY(cp(d_row_ptr, L.rp.get(), sizeof(int) * (n + 1)));
+  CWM_TRY(cp(d_col, L.ci.get(), sizeof(int) * z));
+  CWM_TRY(cp(d_val, L.val.get(), sizeof(double) * z));
+  CWM_TRY(cp(d_v, L.v.get(), sizeof(double) * n));
+  CWM_TRY(cp(d_dl1, L.dl1.get(), sizeof(double) * n));
+  if (level + 1 < (int)h->lev.size()) {
+    CWM_TRY(cp(d_agg, L.agg.get(), sizeof(int) * n));
+    CWM_TRY(cp(d_p, L.p.get(), sizeof(double) * n));
+  }
+  CWM_CUDA(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+amg_status amg_sweep_mate(amg_handle h, int level, int sweep, int32_t *d_mate, int *n, void *stream) {
+  CWM_TRY(validate_handle(h));
+  if (level < 0 || level >= (int)h->lev.size() || sweep < 0 || sweep >= (int)h->lev[level].sweep_mate.size()) {
+    set_error("amg_sweep_mate: no kept matching for level %d sweep %d (keep_sweeps=%d)", level, sweep,
+              h->prm.keep_sweeps);
+    return AMG_ERR_INVALID_ARG;
+  }
+  const Level &L = h->lev[level];
+  const int m = L.sweep_n[sweep];
+  if (n) *n = m;
+  if (d_mate) {
+    CWM_CUDA(cudaStreamSynchronize(h->stream));
+    CWM_CUDA(cudaMemcpyAsync(d_mate, L.sweep_mate[sweep].get(), sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    CWM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  }
+  return AMG_OK;
+}
+
+amg_status amg_vcycle(amg_handle h, const double *d_r, double *d_w, void *stream) {
+  CWM_TRY(validate_handle(h));
+  if (!d_r || !d_w || d_r == d_w) {
+    set_error("amg_vcycle: NULL or aliased vectors");
+    return AMG_ERR_INVALID_ARG;
+  }
+  cudaStream_t prev = h->stream;
+  h->stream = (cudaStream_t)stream;
+  TraceGuard tg(h);
+  amg_status st = apply_vcycle(h, d_r, d_w);
+  h->stream = prev;
+  return st;
+}
+
+amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rtol, int itmax, void *stream,
+                         amg_info *info) {
+  CWM_TRY(validate_handle(h));
+  if (!d_b || !d_x || itmax < 0 || !(rtol >= 0.0)) {
+    set_error("amg_pcg_solve: invalid argument");
+    return AMG_ERR_INVALID_ARG;
+  }
+  const double t0 = now_ms();
+  cudaStream_t prev = h->stream;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  struct Restore {
+    amg_hierarchy *h;
+    cudaStream_t s;
+    ~Restore() { h->stream = s; }
+  } restore{h, prev};
+  TraceGuard tg(h);
+
+  const Level &L0 = h->lev[0];
+  const CsrView<double> A = L0.view64();
+  const int n = L0.n;
+  const int nb = fcg_partial_blocks(n);
+  double *scal = h->scal.get();
+  CWM_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * kFcgSlots, s));
+  CWM_TRY(residual(A, d_b, d_x, h->r.get(), s));
+  CWM_TRY(sqnorm_partials(n, d_b, h->part2.get(), s));
+  CWM_TRY(reduce_into(nb, h->part2.get(), scal, kBB, s));
+  CWM_TRY(sqnorm_partials(n, h->r.get(), h->part2.get(), s));
+  CWM_TRY(reduce_into(nb, h->part2.get(), scal, kRR, s));
+  CWM_CUDA(cudaMemcpyAsync(h->box.dbls, scal, sizeof(double) * kFcgSlots, cudaMemcpyDeviceToHost, s));
+  CWM_CUDA(cudaStreamSynchronize(s));
+  const double nb2 = std::sqrt(h->box.dbls[kBB]);
+  double nr = std::sqrt(h->box.dbls[kRR]);
+  amg_status status = (nb2 == 0.0 || nr <= rtol * nb2) ? AMG_OK : AMG_ERR_NOT_CONVERGED;
+  int it = 0;
+  while (status != AMG_OK && it < itmax) {
+    const int first = it == 0;
+    CWM_TRY(apply_vcycle(h, h->r.get(), h->w.get()));
+    CWM_TRY(spmv_dots(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(), s));
+    CWM_TRY(fcg_scalars(nb, h->part.get(), scal, first, s));
+    CWM_TRY(fcg_update(n, h->w.get(), h->vv.get(), h->d.get(), h->q.get(), d_x, h->r.get(), scal, h->part2.get(),
+                       first, s));
+    CWM_TRY(reduce_into(nb, h->part2.get(), scal, kRR, s));
+    CWM_CUDA(cudaMemcpyAsync(h->box.dbls, scal, sizeof(double) * kFcgSlots, cudaMemcpyDeviceToHost, s));
+    CWM_CUDA(cudaStreamSynchronize(s));
+    if (h->box.dbls[kFlags] != 0.0) {
+      status = AMG_ERR_BREAKDOWN;
+      set_error("amg_pcg_solve: breakdown at iteration %d (rho = %g)", it, h->box.dbls[kRho]);
+      break;
+    }
+    ++it;
+    nr = std::sqrt(h->box.dbls[kRR]);
+    if (nr <= rtol * nb2) status = AMG_OK;
+  }
+  if (status == AMG_ERR_NOT_CONVERGED) set_error("amg_pcg_solve: itmax = %d reached", itmax);
+  // true residual
+  CWM_TRY(residual(A, d_b, d_x, h->vv.get(), s));
+  CWM_TRY(sqnorm_partials(n, h->vv.get(), h->part2.get(), s));
+  CWM_TRY(reduce_into(nb, h->part2.get(), scal, kBB + 0, s));  // reuse slot: true ||r||^2
+  CWM_CUDA(cudaMemcpyAsync(h->box.dbls + 12, scal + kBB, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CWM_CUDA(cudaStreamSynchronize(s));
+  const double nr_true = std::sqrt(h->box.dbls[12]);
+  h->t_solve_ms = now_ms() - t0;
+  if (info) {
+    amg_stats(h, info);
+    info->iters = it;
+    info->rel_res = nb2 > 0.0 ? nr / nb2 : 0.0;
+    info->rel_res_true = nb2 > 0.0 ? nr_true / nb2 : 0.0;
+    info->t_solve_ms = h->t_solve_ms;
+  }
+  return status;
+}
+
+// ------------------------------------------------------------ tracing ----
+amg_status amg_trace_enable(amg_handle h, int on, const char *filter) {
+  CWM_TRY(validate_handle(h));
+  h->trace.on = on != 0;
+  h->trace.filter = filter ? filter : "";
+  return AMG_OK;
+}
+
+amg_status amg_trace_reset(amg_handle h) {
+  CWM_TRY(validate_handle(h));
+  h->trace.flush();
+  h->trace.entries.clear();
+  return AMG_OK;
+}
+
+int amg_trace_count(amg_handle h) {
+  if (!h) return -1;
+  h->trace.flush();
+  return (int)h->trace.entries.size();
+}
+
+amg_status amg_trace_get(amg_handle h, int i, amg_trace_entry *out) {
+  CWM_TRY(validate_handle(h));
+  if (!out || i < 0 || i >= (int)h->trace.entries.size()) {
+    set_error("amg_trace_get: index %d out of range", i);
+    return AMG_ERR_INVALID_ARG;
+  }
+  const TraceEntry &e = h->trace.entries[i];
+  std::memset(out, 0, sizeof(*out));
+  std::strncpy(out->name, e.name.c_str(), sizeof(out->name) - 1);
+  out->launches = e.launches;
+  out->total_ms = e.ms;
+  out->bytes = e.bytes;
+  return AMG_OK;
+}
+
+int64_t amg_launch_count(void) { return cwm::launch_count(); }
+
+// ------------------------------------------------------------ step entry points ----
+static amg_status read_bits(int *d_err, int *h_slot, cudaStream_t s, const char *where) {
+  CWM_CUDA(cudaMemcpyAsync(h_slot, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CWM_CUDA(cudaStreamSynchronize(s));
+  return status_from_device_bits(*h_slot, where);
+}
+
+amg_status cwm_edge_weights(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+                            const double *d_v, double *d_w, void *stream) {
+  if (n < 0 || nnz < 0 || nnz >= (int64_t)INT32_MAX || (n > 0 && (!d_row_ptr || !d_v)) ||
+      (nnz > 0 && (!d_col || !d_val || !d_w))) {
+    set_error("cwm_edge_weights: invalid argument");
+    return AMG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return AMG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<double> diag;
+  DBuf<int> err;
+  int h_err = 0;
+  CWM_TRY(diag.alloc(n, s));
+  CWM_TRY(err.alloc(1, s));
+  CWM_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+  CWM_TRY(extract_diag(n, d_row_ptr, d_col, d_val, diag.get(), err.get(), s));
+  CWM_TRY(edge_weights(n, nnz, d_row_ptr, d_col, d_val, diag.get(), d_v, d_w, s));
+  return read_bits(err.get(), &h_err, s, "cwm_edge_weights");
+}
+
+amg_status cwm_suitor_match(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_w,
+                            int32_t *d_mate, void *stream) {
+  if (n < 0 || nnz < 0 || nnz >= (int64_t)INT32_MAX || (n > 0 && (!d_row_ptr || !d_mate)) ||
+      (nnz > 0 && (!d_col || !d_w))) {
+    set_error("cwm_suitor_match: invalid argument");
+    return AMG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return AMG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<unsigned char> keys;
+  DBuf<int> err;
+  int h_err = 0;
+  CWM_TRY(keys.alloc(suitor_scratch_bytes(n), s));
+  CWM_TRY(err.alloc(1, s));
+  CWM_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+  CWM_TRY(suitor_match(n, nnz, d_row_ptr, d_col, d_w, keys.get(), d_mate, nnz + n + 1024, err.get(), s));
+  return read_bits(err.get(), &h_err, s, "cwm_suitor_match");
+}
+
+amg_status cwm_aggregate(int n, const int32_t *d_mate, const double *d_v, int32_t *d_agg, double *d_p, double *d_vc,
+                         int *h_nc, int *h_npairs, void *stream) {
+  if (n < 0 || (n > 0 && (!d_mate || !d_v || !d_agg || !d_p || !d_vc))) {
+    set_error("cwm_aggregate: invalid argument");
+    return AMG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<int> ids, scan, counts;
+  CWM_TRY(ids.alloc((size_t)n + 1, s));
+  CWM_TRY(scan.alloc(scan_scratch_ints(n), s));
+  CWM_TRY(counts.alloc(2, s));
+  CWM_TRY(aggregate(n, d_mate, d_v, d_agg, d_p, d_vc, nullptr, nullptr, ids.get(), scan.get(), counts.get(), s));
+  int hc[2] = {0, 0};
+  CWM_CUDA(cudaMemcpyAsync(hc, counts.get(), sizeof(hc), cudaMemcpyDeviceToHost, s));
+  CWM_CUDA(cudaStreamSynchronize(s));
+  if (h_nc) *h_nc = hc[0];
+  if (h_npairs) *h_npairs = hc[1];
+  return AMG_OK;
+}
+
+amg_status cwm_galerkin(int n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val, int nc,
+                        const int32_t *d_agg, const double *d_p, int32_t *d_rpc, int32_t *d_colc, double *d_valc,
+                        int64_t capacity, int64_t *h_nnzc, void *stream) {
+  if (n < 0 || nc < 0 || nc > n || (n > 0 && (!d_row_ptr || !d_agg || !d_p)) || !d_rpc || capacity < 0) {
+    set_error("cwm_galerkin: invalid argument");
+    return AMG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<int> m1, m2, cnt, longr, misc, scan, err;
+  CWM_TRY(m1.alloc(nc, s));
+  CWM_TRY(m2.alloc(nc, s));
+  CWM_TRY(cnt.alloc((size_t)nc + 1, s));
+  CWM_TRY(longr.alloc(nc, s));
+  CWM_TRY(misc.alloc(1, s));
+  CWM_TRY(scan.alloc(scan_scratch_ints(nc), s));
+  CWM_TRY(err.alloc(1, s));
+  CWM_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+  CWM_TRY(members_from_agg(n, nc, d_agg, m1.get(), m2.get(), cnt.get(), err.get(), s));
+  int h_err = 0;
+  CWM_TRY(read_bits(err.get(), &h_err, s, "cwm_galerkin (aggregates)"));
+  GalerkinWork gw;
+  gw.cnt = cnt.get();
+  gw.long_rows = longr.get();
+  gw.n_long = misc.get();
+  gw.scan = scan.get();
+  CWM_TRY(galerkin_count(d_row_ptr, d_col, d_val, nc, m1.get(), m2.get(), d_agg, d_p, d_rpc, gw, err.get(), s));
+  int nnzc = 0;
+  CWM_CUDA(cudaMemcpyAsync(&nnzc, d_rpc + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CWM_TRY(read_bits(err.get(), &h_err, s, "cwm_galerkin (count)"));
+  if (h_nnzc) *h_nnzc = nnzc;
+  if (nnzc > capacity) {
+    set_error("cwm_galerkin: nnz(A_c) = %d exceeds capacity %lld", nnzc, (long long)capacity);
+    return AMG_ERR_INVALID_ARG;
+  }
+  if (nnzc > 0 && (!d_colc || !d_valc)) {
+    set_error("cwm_galerkin: NULL output arrays");
+    return AMG_ERR_INVALID_ARG;
+  }
+  CWM_TRY(galerkin_fill(d_row_ptr, d_col, d_val, nc, m1.get(), m2.get(), d_agg, d_p, d_rpc, d_colc, d_valc, nullptr,
+                        nullptr, gw, err.get(), s));
+  return read_bits(err.get(), &h_err, s, "cwm_galerkin (fill)");
+}
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+// coarsen.cu -- one pairwise coarsening sweep: input checks, diagonal, edge weights
+// (Sec. 2.2), Suitor matching (Sec. 3.1), aggregation (Sec. 2.2, Algorithm 2), the
+// orthonormal prolongator (Sec. 2.2), and the composition of sweeps (Sec. 5).
+#include "coarsen.cuh"
+
+namespace cwm {
+
+// ------------------------------------------------------------ input checks ----
+// One thread per row: ascending in-range columns, positive stored diagonal, and (when
+// check_sym) a bit-equal mirror entry for every stored (i, j).
+__global__ void k_check_csr(int n, long long nnz, const int *__restrict__ rp,
+                            const int *__restrict__ ci, const double *__restrict__ val,
+                            int check_sym, int *err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = rp[i], e = rp[i + 1];
+  if (s < 0 || e < s || e > nnz || (i == 0 && s != 0) || (i == n - 1 && e != nnz)) {
+    atomicOr(err, kErrInvalid);
+    return;
+  }
+  bool has_diag = false;
+  for (int k = s; k < e; ++k) {
+    int j = ci[k];
+    if (j < 0 || j >= n || (k > s && j <= ci[k - 1])) { atomicOr(err, kErrInvalid); return; }
+    if (j == i) {
+      has_diag = true;
+      if (!(val[k] > 0.0)) atomicOr(err, kErrNotSpd);
+    }
+    if (check_sym && j != i) {
+      const int rs = rp[j], re = rp[j + 1];
+      if (rs < 0 || re < rs || re > nnz) { atomicOr(err, kErrInvalid); return; }  // row j malformed
+      int lo = rs, hi = re - 1, pos = -1;
+      while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int c = ci[mid];
+        if (c == i) { pos = mid; break; }
+        if (c < i) lo = mid + 1; else hi = mid - 1;
+      }
+      if (pos < 0 || __double_as_longlong(val[pos]) != __double_as_longlong(val[k]))
+        atomicOr(err, kErrInvalid);
+    }
+  }
+  if (!has_diag) atomicOr(err, kErrNotSpd);
+}
+
+amg_status check_input(int n, long long nnz, const int *rp, const int *ci, const double *val,
+                       bool check_sym, int *d_err, cudaStream_t s) {
+  CWM_TRACE("check_input", 4.0 * (n + 1) + 12.0 * nnz, s);
+  k_check_csr<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, nnz, rp, ci, val, check_sym ? 1 : 0, d_err);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// Diagonal by binary search in each (sorted) row; a missing or non-positive diagonal
+// raises kErrNotSpd.
+__global__ void k_diag(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                       const double *__restrict__ val, double *__restrict__ diag, int *err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = rp[i], hi = rp[i + 1] - 1;
+  double d = 0.0;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int c = ci[mid];
+    if (c == i) { d = val[mid]; break; }
+    if (c < i) lo = mid + 1; else hi = mid - 1;
+  }
+  if (!(d > 0.0)) atomicOr(err, kErrNotSpd);
+  diag[i] = d;
+}
+
+amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, double *diag,
+                        int *d_err, cudaStream_t s) {
+  CWM_TRACE("diag", 4.0 * (n + 1) + 20.0 * n, s);
+  k_diag<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, rp, ci, val, diag, d_err);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ edge weights ----
+// Sec. 2.2, C(A, v): one T-lane tile per row; lanes stride over the row's slots.
+// No FMA: every product and sum is an explicit round-to-nearest intrinsic in the
+// order ((2 a) v_a) v_b over ((a_aa v_a) v_a) + ((a_bb v_b) v_b), a = min(i,j).
+template <int T>
+__global__ void __launch_bounds__(256) k_edge_weights(int n, const int *__restrict__ rp,
+                                                      const int *__restrict__ ci,
+                                                      const double *__restrict__ val,
+                                                      const double *__restrict__ diag,
+                                                      const double *__restrict__ v,
+                                                      double *__restrict__ w) {
+  const int lane = threadIdx.x & (T - 1);
+  const long long tile0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  const long long ntiles = (long long)gridDim.x * blockDim.x / T;
+  for (long long row = tile0; row < n; row += ntiles) {
+    const int i = (int)row;
+    const int s = rp[i], e = rp[i + 1];
+    const double vi = v[i], di = diag[i];
+    for (int k = s + lane; k < e; k += T) {
+      const int j = ci[k];
+      const double a = val[k];
+      double c = 0.0;
+      if (j != i && a != 0.0) {
+        const double vj = __ldg(v + j), dj = __ldg(diag + j);
+        const bool lo_i = i < j;
+        const double va = lo_i ? vi : vj, vb = lo_i ? vj : vi;
+        const double da = lo_i ? di : dj, db = lo_i ? dj : di;
+        const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), va), vb);
+        const double den = __dadd_rn(__dmul_rn(__dmul_rn(da, va), va), __dmul_rn(__dmul_rn(db, vb), vb));
+        if (den != 0.0) {
+          const double cc = __dsub_rn(1.0, __ddiv_rn(num, den));
+          if (cc > 0.0) c = cc;
+        }
+      }
+      w[k] = c;
+    }
+  }
+}
+
+amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
+                        const double *diag, const double *v, double *w, cudaStream_t s) {
+  // rp, ci, val, w written; v and diag of each row (gathers of neighbours counted once)
+  CWM_TRACE("weights", 4.0 * (n + 1) + 20.0 * nnz + 16.0 * n, s);
+  const int T = tile_for_mean(n ? (double)nnz / n : 1.0);
+  const int block = 256;
+  const int grid = grid_for((long long)n * T, block, num_sms() * 16);
+  switch (T) {
+    case 4: k_edge_weights<4><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
+    case 8: k_edge_weights<8><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
+    case 16: k_edge_weights<16><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
+    default: k_edge_weights<32><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
+  }
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ Suitor ----
+// Sec. 3.1.  S[x] = (weight bits, suitor + 1) packed in 16 bytes; weights are positive
+// doubles, whose bit patterns order like their values, so the 128-bit pair compares
+// lexicographically as (weight, suitor index).  A proposer u beats the current suitor s
+// of x iff (w_ux, u) > (w_sx, s); u prefers the neighbour maximising (w_ux, x).
+struct __align__(16) SKey {
+  unsigned long long lo;  // suitor index + 1 (0: none)
+  unsigned long long hi;  // weight bits
+};
+
+__device__ __forceinline__ SKey load_key(const SKey *p) {
+  SKey k;
+  asm volatile(
+      "{\n\t.reg .b128 t;\n\t"
+      "ld.relaxed.gpu.global.b128 t, [%2];\n\t"
+      "mov.b128 {%0, %1}, t;\n\t}"
+      : "=l"(k.lo), "=l"(k.hi)
+      : "l"(p)
+      : "memory");
+  return k;
+}
+
+__device__ __forceinline__ bool gt(unsigned long long h1, unsigned long long l1,
+                                   unsigned long long h2, unsigned long long l2) {
+  return h1 > h2 || (h1 == h2 && l1 > l2);
+}
+
+__global__ void k_clear_keys(long long n, SKey *S) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { S[i].lo = 0ull; S[i].hi = 0ull; }
+}
+
+// One T-lane tile per vertex u (grid-stride).  The tile finds the best neighbour that
+// would accept the current proposer, lane 0 installs the proposal with a 128-bit CAS,
+// and a displaced suitor becomes the next proposer (the chain is followed by the same
+// tile).  Every loop is capped; hitting a cap raises kErrTimeout and ends the tile.
+template <int T>
+__global__ void __launch_bounds__(256) k_suitor(int n, const int *__restrict__ rp,
+                                                const int *__restrict__ ci,
+                                                const double *__restrict__ w, SKey *S,
+                                                long long cap, int *err) {
+  auto tile = cg::tiled_partition<T>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const long long tile0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  const long long ntiles = (long long)gridDim.x * blockDim.x / T;
+  for (long long u = tile0; u < n; u += ntiles) {
+    int current = (int)u;
+    long long steps = 0;
+    for (;;) {
+      if (++steps > cap) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        break;
+      }
+      const unsigned long long me = (unsigned long long)current + 1ull;
+      unsigned long long bc = 0ull;
+      int bx = -1;
+      const int s = rp[current], e = rp[current + 1];
+      for (int k = s + lane; k < e; k += T) {
+        const double c = w[k];
+        if (!(c > 0.0)) continue;
+        const int x = ci[k];
+        const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
+        if (cb > bc || (cb == bc && x > bx)) {
+          const SKey cur = load_key(S + x);
+          if (gt(cb, me, cur.hi, cur.lo)) { bc = cb; bx = x; }
+        }
+      }
+#pragma unroll
+      for (int o = T / 2; o > 0; o >>= 1) {
+        const unsigned long long oc = tile.shfl_xor(bc, o);
+        const int ox = tile.shfl_xor(bx, o);
+        if (oc > bc || (oc == bc && ox > bx)) { bc = oc; bx = ox; }
+      }
+      if (bx < 0) break;  // nobody would accept `current`: it stays unmatched
+      int next = -2;      // -2: beaten while proposing, rescan
+      if (lane == 0) {
+        SKey mine;
+        mine.lo = me;
+        mine.hi = bc;
+        SKey expect = load_key(S + bx);
+        for (int t = 0; t < (1 << 22); ++t) {
+          if (!gt(bc, me, expect.hi, expect.lo)) break;
+          const SKey old = atomicCAS(S + bx, expect, mine);
+          if (old.lo == expect.lo && old.hi == expect.hi) {
+            next = (int)old.lo - 1;  // -1: x had no suitor
+            break;
+          }
+          expect = old;
+        }
+      }
+      next = tile.shfl(next, 0);
+      if (next == -2) continue;
+      if (next < 0) break;
+      current = next;
+    }
+  }
+}
+
+__global__ void k_suitor_mate(int n, const SKey *__restrict__ S, int *__restrict__ mate) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = (int)S[i].lo - 1;
+  mate[i] = (s >= 0 && (int)S[s].lo - 1 == i) ? s : -1;
+}
+
+size_t suitor_scratch_bytes(int n) { return (size_t)n * sizeof(SKey); }
+
+amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, const double *w,
+                        void *scratch, int *mate, long long cap, int *d_err, cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  // one proposal pass: rp, ci, w; S cleared, read once per vertex, read for the mates; mate
+  CWM_TRACE("suitor", 4.0 * (n + 1) + 12.0 * nnz + 52.0 * n, s);
+  SKey *S = reinterpret_cast<SKey *>(scratch);
+  k_clear_keys<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, S);
+  CWM_LAUNCH();
+  if (cap <= 0) cap = nnz + (long long)n + 1024;
+  const int T = tile_for_mean(n ? (double)nnz / n : 1.0);
+  const int block = 256;
+  const int grid = grid_for((long long)n * T, block, num_sms() * 8);
+  switch (T) {
+    case 4: k_suitor<4><<<grid, block, 0, s>>>(n, rp, ci, w, S, cap, d_err); break;
+    case 8: k_suitor<8><<<grid, block, 0, s>>>(n, rp, ci, w, S, cap, d_err); break;
+    case 16: k_suitor<16><<<grid, block, 0, s>>>(n, rp, ci, w, S, cap, d_err); break;
+    default: k_suitor<32><<<grid, block, 0, s>>>(n, rp, ci, w, S, cap, d_err); break;
+  }
+  CWM_LAUNCH();
+  k_suitor_mate<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, S, mate);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ aggregation ----
+// Sec. 2.2, Algorithm 2 with U scanned in ascending order: vertex i starts an aggregate
+// iff it is unmatched or the smaller end of its pair, and the aggregate id is the number
+// of such leaders before i (an exclusive scan).  The leader writes both members' agg
+// and p, v_c, and the member list.
+__global__ void k_leader_flags(int n, const int *__restrict__ mate, int *__restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m = mate[i];
+  flag[i] = (m < 0 || i < m) ? 1 : 0;
+}
+
+// pairs counted with one atomic per block
+__global__ void k_count_pairs(int n, const int *__restrict__ mate, int *npairs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int is_pair = (i < n && mate[i] > i) ? 1 : 0;
+  int c = __syncthreads_count(is_pair);
+  if (threadIdx.x == 0 && c) atomicAdd(npairs, c);
+}
+
+__global__ void k_aggregate_fill(int n, const int *__restrict__ mate, const int *__restrict__ id,
+                                 const double *__restrict__ v, int *__restrict__ agg,
+                                 double *__restrict__ p, double *__restrict__ vc,
+                                 int *__restrict__ m1, int *__restrict__ m2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int j = mate[i];
+  if (j >= 0 && j < i) return;  // the follower is written by its leader
+  const int I = id[i];
+  const double vi = v[i];
+  agg[i] = I;
+  if (m1) m1[I] = i;
+  if (j > i) {
+    const double vj = v[j];
+    const double s = __dsqrt_rn(__dadd_rn(__dmul_rn(vi, vi), __dmul_rn(vj, vj)));
+    p[i] = __ddiv_rn(vi, s);
+    p[j] = __ddiv_rn(vj, s);
+    agg[j] = I;
+    vc[I] = s;
+    if (m2) m2[I] = j;
+  } else {
+    const double a = fabs(vi);
+    p[i] = a > 0.0 ? __ddiv_rn(vi, a) : 1.0;
+    vc[I] = a;
+    if (m2) m2[I] = -1;
+  }
+}
+
+amg_status aggregate(int n, const int *mate, const double *v, int *agg, double *p, double *vc,
+                     int *m1, int *m2, int *id_scratch, int *scan_scratch, int *d_counts,
+                     cudaStream_t s) {
+  // d_counts[0] = n_c, d_counts[1] = n_pairs
+  CWM_CUDA(cudaMemsetAsync(d_counts, 0, 2 * sizeof(int), s));
+  if (n == 0) return AMG_OK;
+  CWM_TRACE("aggregate", 52.0 * n, s);
+  const int g = grid_for(n, 256, 1 << 30);
+  k_leader_flags<<<g, 256, 0, s>>>(n, mate, id_scratch);
+  CWM_LAUNCH();
+  k_count_pairs<<<g, 256, 0, s>>>(n, mate, d_counts + 1);
+  CWM_LAUNCH();
+  CWM_TRY(exclusive_scan(id_scratch, id_scratch, n, scan_scratch, s));
+  CWM_CUDA(cudaMemcpyAsync(d_counts, id_scratch + n, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  k_aggregate_fill<<<g, 256, 0, s>>>(n, mate, id_scratch, v, agg, p, vc, m1, m2);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ composition ----
+// Row i of P_1 ... P_S has column agg_S[...agg_1[i]] and value
+// ((p_1[i] * p_2[agg_1[i]]) * p_3[agg_2[agg_1[i]]]) ..., multiplied left to right.
+__global__ void k_compose(int n, SweepMaps maps, int *__restrict__ agg_out, double *__restrict__ p_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = maps.agg[0][i];
+  double pp = maps.p[0][i];
+  for (int s = 1; s < maps.count; ++s) {
+    pp = __dmul_rn(pp, maps.p[s][a]);
+    a = maps.agg[s][a];
+  }
+  agg_out[i] = a;
+  p_out[i] = pp;
+}
+
+amg_status compose(int n, const SweepMaps &maps, int *agg_out, double *p_out, cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  CWM_TRACE("compose", 24.0 * n, s);
+  k_compose<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, maps, agg_out, p_out);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ member lists ----
+// The transpose of the composed P as lists: members of aggregate I in ascending order
+// (count, scan, scatter, then a tiny insertion sort per list, so the order does not
+// depend on the scatter's atomics).
+__global__ void k_count_members(int n, const int *__restrict__ agg, int *__restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(cnt + agg[i], 1);
+}
+
+__global__ void k_scatter_members(int n, const int *__restrict__ agg, const int *__restrict__ mptr,
+                                  int *__restrict__ cursor, int *__restrict__ mlist) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int I = agg[i];
+  const int pos = atomicAdd(cursor + I, 1);
+  mlist[mptr[I] + pos] = i;
+}
+
+__global__ void k_sort_members(int nc, const int *__restrict__ mptr, int *__restrict__ mlist) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  const int s = mptr[I], e = mptr[I + 1];
+  for (int a = s + 1; a < e; ++a) {
+    const int x = mlist[a];
+    int b = a - 1;
+    while (b >= s && mlist[b] > x) { mlist[b + 1] = mlist[b]; --b; }
+    mlist[b + 1] = x;
+  }
+}
+
+amg_status member_lists(int n, int nc, const int *agg, int *mptr, int *mlist, int *cnt_scratch,
+                        int *scan_scratch, cudaStream_t s) {
+  CWM_TRACE("members", 16.0 * n + 16.0 * nc, s);
+  CWM_CUDA(cudaMemsetAsync(cnt_scratch, 0, sizeof(int) * ((size_t)nc + 1), s));
+  const int g = grid_for(n, 256, 1 << 30);
+  k_count_members<<<g, 256, 0, s>>>(n, agg, cnt_scratch);
+  CWM_LAUNCH();
+  CWM_TRY(exclusive_scan(cnt_scratch, mptr, nc, scan_scratch, s));
+  CWM_CUDA(cudaMemsetAsync(cnt_scratch, 0, sizeof(int) * ((size_t)nc + 1), s));
+  k_scatter_members<<<g, 256, 0, s>>>(n, agg, mptr, cnt_scratch, mlist);
+  CWM_LAUNCH();
+  k_sort_members<<<grid_for(nc, 256, 1 << 30), 256, 0, s>>>(nc, mptr, mlist);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+}  // namespace cwm

@@ -1,0 +1,58 @@
+// coarsen.cuh -- host launchers of the coarsening kernels (coarsen.cu, galerkin.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace cwm {
+
+constexpr int kMaxSweeps = 8;
+
+// Per-sweep aggregate maps and prolongator values, passed by value to k_compose.
+struct SweepMaps {
+  const int *agg[kMaxSweeps];
+  const double *p[kMaxSweeps];
+  int count;
+};
+
+amg_status check_input(int n, long long nnz, const int *rp, const int *ci, const double *val,
+                       bool check_sym, int *d_err, cudaStream_t s);
+amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, double *diag,
+                        int *d_err, cudaStream_t s);
+amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
+                        const double *diag, const double *v, double *w, cudaStream_t s);
+size_t suitor_scratch_bytes(int n);
+amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, const double *w,
+                        void *scratch, int *mate, long long cap, int *d_err, cudaStream_t s);
+// d_counts[0] <- n_c, d_counts[1] <- number of pairs.  id_scratch: n+1 ints.
+amg_status aggregate(int n, const int *mate, const double *v, int *agg, double *p, double *vc,
+                     int *m1, int *m2, int *id_scratch, int *scan_scratch, int *d_counts,
+                     cudaStream_t s);
+amg_status compose(int n, const SweepMaps &maps, int *agg_out, double *p_out, cudaStream_t s);
+// cnt_scratch: nc+1 ints.
+amg_status member_lists(int n, int nc, const int *agg, int *mptr, int *mlist, int *cnt_scratch,
+                        int *scan_scratch, cudaStream_t s);
+
+// Galerkin product for a pairwise P (galerkin.cu).
+struct GalerkinWork {
+  int *cnt = nullptr;        // nc + 1 ints (row counts, then row pointers are written to rpc)
+  int *long_rows = nullptr;  // nc ints: coarse rows too long for the warp kernel
+  int *n_long = nullptr;     // 1 int
+  int *scan = nullptr;       // scan scratch
+  int n_fine = 0;            // fine size and nnz (for the tracer's byte counts)
+  long long nnz_fine = 0;
+};
+// Pass 1: row counts of A_c, scanned into rpc (rpc[nc] = nnz(A_c) on the device).
+amg_status galerkin_count(const int *rp, const int *ci, const double *val, int nc, const int *m1,
+                          const int *m2, const int *agg, const double *p, int *rpc,
+                          const GalerkinWork &work, int *d_err, cudaStream_t s);
+// Pass 2: columns and values of A_c at rpc; diag_c (nc) and dl1_c (nc) may be NULL.
+amg_status galerkin_fill(const int *rp, const int *ci, const double *val, int nc, const int *m1,
+                         const int *m2, const int *agg, const double *p, const int *rpc, int *cic,
+                         double *valc, double *diag_c, double *dl1_c, const GalerkinWork &work,
+                         int *d_err, cudaStream_t s);
+// m1/m2 from agg when the caller only has agg (cwm_galerkin): members in ascending order;
+// an empty aggregate or one with more than two members raises kErrInvalid.  cnt: nc ints.
+amg_status members_from_agg(int n, int nc, const int *agg, int *m1, int *m2, int *cnt, int *d_err,
+                            cudaStream_t s);
+
+}  // namespace cwm

@@ -1,0 +1,143 @@
+// common.cuh -- shared host/device utilities of the CUDA path (errors, buffers, scans).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <utility>
+
+#include "cwm_amg.h"
+
+namespace cwm {
+
+namespace cg = cooperative_groups;
+
+// Device-side error word bits (OR-ed by kernels, read by the host after a sync).
+enum : int {
+  kErrTimeout = 1,      // a bounded retry loop hit its cap
+  kErrNotSpd = 2,       // missing or non-positive diagonal
+  kErrInvalid = 4,      // malformed CSR, asymmetric A, aggregate with > 2 members
+  kErrUnsupported = 8,  // a Galerkin row beyond the long-row capacity
+  kErrBreakdown = 16,   // FCG rho <= 0 or not finite
+};
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const char *fmt, ...);
+amg_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+amg_status status_from_device_bits(int bits, const char *where);
+
+#define CWM_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) return ::cwm::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define CWM_TRY(expr)                        \
+  do {                                       \
+    amg_status s_ = (expr);                  \
+    if (s_ != AMG_OK) return s_;             \
+  } while (0)
+
+// Launch-error check after a kernel launch; also counts the library's kernel launches.
+void count_launch();
+#define CWM_LAUNCH()         \
+  do {                       \
+    ::cwm::count_launch();   \
+    CWM_CUDA(cudaGetLastError()); \
+  } while (0)
+long long launch_count();
+
+// ---------------------------------------------------------------- tracing ----
+// Optional per-kernel-class timing with CUDA events recorded on the launching stream
+// around each launch, plus the algorithmic bytes each launch moves.  Active only while a
+// handle's tracer is installed for the calling thread (see amg_trace_enable).
+struct Tracer;
+extern thread_local Tracer *g_tracer;
+extern thread_local int g_trace_level;  // appended to category names as @k when >= 0
+struct TraceScope {
+  Tracer *t = nullptr;
+  int idx = -1;
+  cudaEvent_t a = nullptr;
+  cudaStream_t s = nullptr;
+  double bytes = 0.0;
+  TraceScope(const char *cat, double bytes, cudaStream_t s);
+  ~TraceScope();
+};
+#define CWM_TRACE(cat, bytes, stream) ::cwm::TraceScope cwm_trace_scope_((cat), (double)(bytes), (stream))
+
+// ---------------------------------------------------------------- buffers ----
+// When set (while a handle is destroyed), buffers are freed synchronously instead of on
+// the stream they were allocated on, which the caller may have destroyed meanwhile.
+extern thread_local bool g_sync_free;
+
+// A stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+  DBuf &operator=(DBuf &&o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  amg_status alloc(size_t count, cudaStream_t stream) {
+    release();
+    s = stream;
+    n = count;
+    if (count == 0) return AMG_OK;
+    cudaError_t e = cudaMallocAsync((void **)&p, count * sizeof(T), stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      (void)cudaGetLastError();
+      set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return AMG_ERR_OOM;
+    }
+    return AMG_OK;
+  }
+  void release() {
+    if (p) {
+      if (g_sync_free) cudaFree(p);
+      else cudaFreeAsync(p, s);
+    }
+    p = nullptr;
+    n = 0;
+  }
+  T *get() const { return p; }
+};
+
+// Makes the device's default memory pool keep freed memory (repeated setups reuse it).
+void retain_pool_memory();
+
+// ---------------------------------------------------------------- launch ----
+int num_sms();
+// Grid for `items` work items of `per_block` items each, capped at `waves` full waves.
+inline int grid_for(long long items, int per_block, int cap_blocks) {
+  long long b = (items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap_blocks) b = cap_blocks;
+  return (int)b;
+}
+// Sub-warp ("miniwarp") width for rows of `mean` stored entries: 4, 8, 16 or 32.
+inline int tile_for_mean(double mean) {
+  if (mean <= 4.5) return 4;
+  if (mean <= 9.0) return 8;
+  if (mean <= 18.0) return 16;
+  return 32;
+}
+
+// ---------------------------------------------------------------- scans ----
+// out[0..n] = exclusive prefix sums of in[0..n) with out[n] = total (int32; the total
+// must fit).  scratch: at least scan_scratch_ints(n) ints.
+size_t scan_scratch_ints(long long n);
+amg_status exclusive_scan(const int *in, int *out, long long n, int *scratch, cudaStream_t s);
+
+}  // namespace cwm

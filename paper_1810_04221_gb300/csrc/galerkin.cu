@@ -1,0 +1,375 @@
+// galerkin.cu -- Galerkin product A_c = P^T A P (Sec. 2.1; the costliest setup step per
+// Sec. 3.1) for the pairwise P of one matching sweep, in two passes (count, fill).
+//
+// Coarse row I has members i1 < i2 (or i1 alone).  The fine entries of rows i1 and i2 are
+// keyed by (J = agg(j), local slot) and sorted in shared memory (bitonic), so equal J are
+// adjacent.  Each run of equal J holds at most four terms (two members each side); the
+// run's value sums t_ij = (p_i p_j) a_ij from +0.0 in ascending (min(i,j), max(i,j), i)
+// order with round-to-nearest intrinsics, which makes the result independent of the
+// thread schedule and bit-symmetric.  Rows gathering more than kWarpCap entries go to a
+// block-per-row kernel (up to kBlockCap entries).
+#include <climits>
+
+#include "coarsen.cuh"
+
+namespace cwm {
+
+constexpr int kWarpCap = 256;     // keys per warp in shared memory
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlockCap = 8192;   // keys per long row (64 KB of dynamic shared memory)
+constexpr int kLongThreads = 256;
+
+struct RowSrc {
+  int i1, i2;  // members (i2 < 0: singleton)
+  int s1, L1;  // first slot and length of row i1
+  int s2, L2;  // same for row i2
+};
+
+__device__ __forceinline__ RowSrc row_src(int I, const int *__restrict__ m1, const int *__restrict__ m2,
+                                          const int *__restrict__ rp) {
+  RowSrc r;
+  r.i1 = m1[I];
+  r.i2 = m2[I];
+  r.s1 = rp[r.i1];
+  r.L1 = rp[r.i1 + 1] - r.s1;
+  if (r.i2 >= 0) {
+    r.s2 = rp[r.i2];
+    r.L2 = rp[r.i2 + 1] - r.s2;
+  } else {
+    r.s2 = 0;
+    r.L2 = 0;
+  }
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long make_key(const RowSrc &r, int q, const int *__restrict__ ci,
+                                                       const int *__restrict__ agg) {
+  const int k = q < r.L1 ? r.s1 + q : r.s2 + (q - r.L1);
+  const unsigned J = (unsigned)agg[ci[k]];
+  return ((unsigned long long)J << 32) | (unsigned)q;
+}
+
+// Sum of one run of equal J (length len <= 4) starting at sorted position q.
+__device__ __forceinline__ double run_value(const RowSrc &r, const unsigned long long *keys, int q, int len,
+                                            const int *__restrict__ ci, const double *__restrict__ val,
+                                            const double *__restrict__ p) {
+  int kmin[4], kmax[4], ii[4];
+  double t[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (e < len) {
+      const int local = (int)(keys[q + e] & 0xffffffffu);
+      const bool first = local < r.L1;
+      const int i = first ? r.i1 : r.i2;
+      const int k = first ? r.s1 + local : r.s2 + (local - r.L1);
+      const int j = ci[k];
+      t[e] = __dmul_rn(__dmul_rn(p[i], p[j]), val[k]);
+      kmin[e] = i < j ? i : j;
+      kmax[e] = i < j ? j : i;
+      ii[e] = i;
+    } else {
+      t[e] = 0.0;
+      kmin[e] = kmax[e] = ii[e] = INT_MAX;
+    }
+  }
+  // insertion sort of <= 4 terms by (kmin, kmax, i)
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+#pragma unroll
+    for (int b = a; b > 0; --b) {
+      const bool swap = kmin[b] < kmin[b - 1] ||
+                        (kmin[b] == kmin[b - 1] && (kmax[b] < kmax[b - 1] ||
+                                                    (kmax[b] == kmax[b - 1] && ii[b] < ii[b - 1])));
+      if (swap) {
+        int x;
+        double y;
+        x = kmin[b]; kmin[b] = kmin[b - 1]; kmin[b - 1] = x;
+        x = kmax[b]; kmax[b] = kmax[b - 1]; kmax[b - 1] = x;
+        x = ii[b]; ii[b] = ii[b - 1]; ii[b - 1] = x;
+        y = t[b]; t[b] = t[b - 1]; t[b - 1] = y;
+      }
+    }
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (e < len) sum = __dadd_rn(sum, t[e]);
+  return sum;
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// ------------------------------------------------------------ warp kernel ----
+// FILL = false: cnt[I] = number of distinct J; long rows are queued.
+// FILL = true:  writes columns and values at rpc[I]; diag_c / dl1_c when given.
+template <bool FILL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_galerkin_warp(int nc, const int *__restrict__ rp, const int *__restrict__ ci,
+                    const double *__restrict__ val, const int *__restrict__ m1,
+                    const int *__restrict__ m2, const int *__restrict__ agg,
+                    const double *__restrict__ p, int *__restrict__ cnt,
+                    const int *__restrict__ rpc, int *__restrict__ cic, double *__restrict__ valc,
+                    double *__restrict__ diag_c, double *__restrict__ dl1_c,
+                    int *__restrict__ long_rows, int *__restrict__ n_long, int *err) {
+  __shared__ unsigned long long sbuf[kWarpsPerBlock][kWarpCap];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  unsigned long long *keys = sbuf[wib];
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long row = warp0; row < nc; row += nwarps) {
+    const int I = (int)row;
+    const RowSrc r = row_src(I, m1, m2, rp);
+    const int L = r.L1 + r.L2;
+    if (L > kWarpCap) {
+      if (!FILL && lane == 0) long_rows[atomicAdd(n_long, 1)] = I;
+      continue;
+    }
+    const int P = next_pow2(L < 32 ? 32 : L);
+    for (int q = lane; q < P; q += 32) keys[q] = q < L ? make_key(r, q, ci, agg) : ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = lane; q < P; q += 32) {
+          const int l = q ^ j;
+          if (l > q) {
+            const unsigned long long a = keys[q], b = keys[l];
+            if ((a > b) == ((q & k) == 0)) { keys[q] = b; keys[l] = a; }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    int base = 0;
+    double l1 = 0.0;
+    for (int q0 = 0; q0 < L; q0 += 32) {
+      const int q = q0 + lane;
+      bool head = false;
+      unsigned J = 0;
+      if (q < L) {
+        J = (unsigned)(keys[q] >> 32);
+        head = q == 0 || (unsigned)(keys[q - 1] >> 32) != J;
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, head);
+      if (FILL && head) {
+        int len = 1;
+        while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
+        if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
+        const double s = run_value(r, keys, q, len, ci, val, p);
+        const int out = rpc[I] + base + __popc(ball & ((1u << lane) - 1u));
+        cic[out] = (int)J;
+        valc[out] = s;
+        if ((int)J == I && diag_c) diag_c[I] = s;
+        l1 += fabs(s);
+      }
+      base += __popc(ball);
+    }
+    if (!FILL) {
+      if (lane == 0) cnt[I] = base;
+    } else if (dl1_c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+      if (lane == 0) dl1_c[I] = l1;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ long rows ----
+template <bool FILL>
+__global__ void __launch_bounds__(kLongThreads)
+    k_galerkin_block(const int *__restrict__ rp, const int *__restrict__ ci,
+                     const double *__restrict__ val, const int *__restrict__ m1,
+                     const int *__restrict__ m2, const int *__restrict__ agg,
+                     const double *__restrict__ p, int *__restrict__ cnt,
+                     const int *__restrict__ rpc, int *__restrict__ cic, double *__restrict__ valc,
+                     double *__restrict__ diag_c, double *__restrict__ dl1_c,
+                     const int *__restrict__ long_rows, const int *__restrict__ n_long, int *err) {
+  extern __shared__ unsigned long long keys[];
+  __shared__ int wsum[kLongThreads / 32 + 1];
+  __shared__ double wl1[kLongThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kLongThreads / 32;
+  const int nrows = *n_long;
+  for (int b = blockIdx.x; b < nrows; b += gridDim.x) {
+    const int I = long_rows[b];
+    const RowSrc r = row_src(I, m1, m2, rp);
+    const int L = r.L1 + r.L2;
+    if (L > kBlockCap) {
+      if (tid == 0) {
+        atomicOr(err, kErrUnsupported);
+        if (!FILL) cnt[I] = 0;
+      }
+      continue;
+    }
+    const int P = next_pow2(L < kLongThreads ? kLongThreads : L);
+    for (int q = tid; q < P; q += kLongThreads) keys[q] = q < L ? make_key(r, q, ci, agg) : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = tid; q < P; q += kLongThreads) {
+          const int l = q ^ j;
+          if (l > q) {
+            const unsigned long long a = keys[q], bb = keys[l];
+            if ((a > bb) == ((q & k) == 0)) { keys[q] = bb; keys[l] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    int base = 0;
+    double l1 = 0.0;
+    for (int q0 = 0; q0 < L; q0 += kLongThreads) {
+      const int q = q0 + tid;
+      bool head = false;
+      unsigned J = 0;
+      if (q < L) {
+        J = (unsigned)(keys[q] >> 32);
+        head = q == 0 || (unsigned)(keys[q - 1] >> 32) != J;
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, head);
+      if (lane == 0) wsum[warp] = __popc(ball);
+      __syncthreads();
+      int before = 0, chunk = 0;
+      for (int w = 0; w < nw; ++w) {
+        if (w < warp) before += wsum[w];
+        chunk += wsum[w];
+      }
+      if (FILL && head) {
+        int len = 1;
+        while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
+        if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
+        const double s = run_value(r, keys, q, len, ci, val, p);
+        const int out = rpc[I] + base + before + __popc(ball & ((1u << lane) - 1u));
+        cic[out] = (int)J;
+        valc[out] = s;
+        if ((int)J == I && diag_c) diag_c[I] = s;
+        l1 += fabs(s);
+      }
+      base += chunk;
+      __syncthreads();
+    }
+    if (!FILL) {
+      if (tid == 0) cnt[I] = base;
+    } else if (dl1_c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+      if (lane == 0) wl1[warp] = l1;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += wl1[w];
+        dl1_c[I] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static amg_status galerkin_attrs() {
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  CWM_CUDA(cudaGetDevice(&dev));
+  bool &attr = attr_set[dev & 63];
+  if (!attr) {
+    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kBlockCap * 8));
+    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kBlockCap * 8));
+    attr = true;
+  }
+  return AMG_OK;
+}
+
+amg_status galerkin_count(const int *rp, const int *ci, const double *val, int nc, const int *m1,
+                          const int *m2, const int *agg, const double *p, int *rpc,
+                          const GalerkinWork &work, int *d_err, cudaStream_t s) {
+  if (nc == 0) {
+    CWM_CUDA(cudaMemsetAsync(rpc, 0, sizeof(int), s));
+    return AMG_OK;
+  }
+  CWM_TRY(galerkin_attrs());
+  // members and row bounds, ci and agg(ci) of both member rows, counts, scan
+  CWM_TRACE("galerkin_count", 4.0 * work.nnz_fine + 4.0 * work.n_fine + 40.0 * nc, s);
+  const int block = kWarpsPerBlock * 32;
+  const int grid = grid_for((long long)nc * 32, block, num_sms() * 8);
+  CWM_CUDA(cudaMemsetAsync(work.n_long, 0, sizeof(int), s));
+  k_galerkin_warp<false><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, nullptr,
+                                                nullptr, nullptr, nullptr, nullptr, work.long_rows,
+                                                work.n_long, d_err);
+  CWM_LAUNCH();
+  k_galerkin_block<false><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+      rp, ci, val, m1, m2, agg, p, work.cnt, nullptr, nullptr, nullptr, nullptr, nullptr,
+      work.long_rows, work.n_long, d_err);
+  CWM_LAUNCH();
+  return exclusive_scan(work.cnt, rpc, nc, work.scan, s);
+}
+
+amg_status galerkin_fill(const int *rp, const int *ci, const double *val, int nc, const int *m1,
+                         const int *m2, const int *agg, const double *p, const int *rpc, int *cic,
+                         double *valc, double *diag_c, double *dl1_c, const GalerkinWork &work,
+                         int *d_err, cudaStream_t s) {
+  if (nc == 0) return AMG_OK;
+  CWM_TRY(galerkin_attrs());
+  // reads as in the count pass plus val and p; writes of A_c not included (size unknown here)
+  CWM_TRACE("galerkin_fill", 12.0 * work.nnz_fine + 12.0 * work.n_fine + 44.0 * nc, s);
+  const int block = kWarpsPerBlock * 32;
+  const int grid = grid_for((long long)nc * 32, block, num_sms() * 8);
+  k_galerkin_warp<true><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic,
+                                               valc, diag_c, dl1_c, nullptr, nullptr, d_err);
+  CWM_LAUNCH();
+  k_galerkin_block<true><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+      rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic, valc, diag_c, dl1_c, work.long_rows,
+      work.n_long, d_err);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ members from agg ----
+__global__ void k_members_init(int nc, int *m1, int *m2, int *cnt) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < nc) { m1[I] = INT_MAX; m2[I] = -1; cnt[I] = 0; }
+}
+
+__global__ void k_members_scatter(int n, int nc, const int *__restrict__ agg, int *m1, int *m2, int *cnt,
+                                  int *err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int I = agg[i];
+  if (I < 0 || I >= nc) { atomicOr(err, kErrInvalid); return; }
+  atomicMin(m1 + I, i);
+  atomicMax(m2 + I, i);
+  atomicAdd(cnt + I, 1);
+}
+
+__global__ void k_members_final(int nc, int *m1, int *m2, const int *cnt, int *err) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  const int c = cnt[I];
+  if (c < 1 || c > 2) {
+    atomicOr(err, kErrInvalid);
+    m1[I] = 0;
+    m2[I] = -1;
+    return;
+  }
+  if (c == 1) m2[I] = -1;
+}
+
+amg_status members_from_agg(int n, int nc, const int *agg, int *m1, int *m2, int *cnt, int *d_err,
+                            cudaStream_t s) {
+  if (nc == 0) return AMG_OK;
+  k_members_init<<<grid_for(nc, 256, 1 << 30), 256, 0, s>>>(nc, m1, m2, cnt);
+  CWM_LAUNCH();
+  if (n > 0) {
+    k_members_scatter<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, nc, agg, m1, m2, cnt, d_err);
+    CWM_LAUNCH();
+  }
+  k_members_final<<<grid_for(nc, 256, 1 << 30), 256, 0, s>>>(nc, m1, m2, cnt, d_err);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+}  // namespace cwm

@@ -1,0 +1,66 @@
+// solve.cuh -- host launchers of the solve-phase kernels (solve.cu): CSR SpMV family,
+// l1-Jacobi (Sec. 3.2), restriction / prolongation with the aggregation P (Sec. 3.2),
+// the one-block coarsest solve, and the flexible-CG vector kernels (Sec. 3.2, Algorithm 3).
+#pragma once
+
+#include "common.cuh"
+
+namespace cwm {
+
+template <class V>
+struct CsrView {
+  int n = 0;
+  long long nnz = 0;
+  const int *rp = nullptr;
+  const int *ci = nullptr;
+  const V *val = nullptr;
+  int tile = 8;  // sub-warp width chosen from the mean row length
+};
+
+// Largest coarsest level solved by the one-block kernel (x kept in shared memory).
+constexpr int kCoarseBlockMax = 2048;
+
+// y = dinv .* b
+template <class V>
+amg_status scale(int n, const V *dinv, const V *b, V *y, cudaStream_t s);
+// y = x + dinv .* (b - A x)   (x, y distinct)
+template <class V>
+amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V *y, cudaStream_t s);
+// bc[I] = sum_{m in I} p_m (b_m - (A x)_m), members mlist[mptr[I] .. mptr[I+1]); x may be NULL (0)
+template <class V>
+amg_status resid_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
+                          const V *b, const V *x, V *bc, cudaStream_t s);
+// y = x + p .* xc[agg]; x may be NULL (0)
+template <class V>
+amg_status prolong(int n, const int *agg, const V *p, const V *xc, const V *x, V *y, cudaStream_t s);
+// x = `sweeps` l1-Jacobi sweeps from zero on a level with n <= kCoarseBlockMax
+template <class V>
+amg_status coarse_solve_block(const CsrView<V> &A, const V *dinv, const V *b, V *x, int sweeps,
+                              cudaStream_t s);
+// r = b - A x
+amg_status residual(const CsrView<double> &A, const double *b, const double *x, double *r, cudaStream_t s);
+
+// FCG device scalars (one array of doubles on the device).
+enum FcgSlot { kAlpha = 0, kBeta, kGamma, kRho, kRhoPrev, kCoef, kStep, kRR, kBB, kFlags, kFcgSlots };
+int fcg_partial_blocks(int n);
+// v = A w and per-block partial sums of w.r, w.v, w.q (q may be NULL) into part[3 * nb]
+amg_status spmv_dots(const CsrView<double> &A, const double *w, const double *r, const double *q, double *v,
+                     double *part, cudaStream_t s);
+// scalars from the partials: alpha, beta, gamma, rho, coef = gamma/rho_prev, step = alpha/rho
+amg_status fcg_scalars(int nb, const double *part, double *scal, int first, cudaStream_t s);
+// d = w - coef d; q = v - coef q; x += step d; r -= step q; partial sums of r.r into part[nb]
+amg_status fcg_update(int n, const double *w, const double *v, double *d, double *q, double *x, double *r,
+                      const double *scal, double *part, int first, cudaStream_t s);
+// scal[slot] = sum of part[0..nb)
+amg_status reduce_into(int nb, const double *part, double *scal, int slot, cudaStream_t s);
+// partial sums of a.a into part[nb]
+amg_status sqnorm_partials(int n, const double *a, double *part, cudaStream_t s);
+// d[i] = sum_j |a_ij| (l1 row norms, Sec. 3.2)
+amg_status l1_norms(const CsrView<double> &A, double *d, cudaStream_t s);
+// y = 1 / x (and a float copy when y32 is not NULL)
+amg_status reciprocal(int n, const double *x, double *y, float *y32, cudaStream_t s);
+// float64 <-> float32 copies
+amg_status to_float(long long n, const double *x, float *y, cudaStream_t s);
+amg_status to_double(long long n, const float *x, double *y, cudaStream_t s);
+
+}  // namespace cwm

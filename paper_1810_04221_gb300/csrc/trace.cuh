@@ -1,0 +1,37 @@
+// trace.cuh -- the per-kernel-class event tracer behind CWM_TRACE (common.cuh).
+#pragma once
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cwm {
+
+struct TraceEntry {
+  std::string name;
+  long long launches;
+  double ms;
+  double bytes;
+};
+
+struct Tracer {
+  bool on = false;
+  std::string filter;  // category prefix; empty = every category
+  std::vector<TraceEntry> entries;
+  struct Pending {
+    int idx;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  ~Tracer();
+  bool wants(const char *cat) const;
+  int entry(const char *cat);
+  cudaEvent_t event();
+  void flush();  // waits for the recorded events and folds them into `entries`
+};
+
+}  // namespace cwm
