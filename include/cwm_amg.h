@@ -152,6 +152,24 @@ amg_status cwm_edge_weights(int n, int64_t nnz, const int32_t *d_row_ptr, const 
 amg_status cwm_suitor_match(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
                             const double *d_w, int32_t *d_mate, void *stream);
 
+/* cwm_suitor_match for callers that cannot allocate device memory -- code running where
+ * cudaMalloc is forbidden or would stall (a real-time loop, a host callback, a process
+ * whose device memory is owned by another allocator or reserved up front).  The paper has
+ * no counterpart: this is an interface variant, not a step of the method.
+ * Same arguments, result and errors as cwm_suitor_match, but the 16 bytes of scratch per
+ * vertex come from a fixed array inside the library (16 MiB, held by every GPU that loads
+ * the library until the process exits), so no call allocates or frees device memory.
+ *   - n is limited to 1,048,576 vertices; larger n returns AMG_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address for that device;
+ *     make that first call before any stream capture.
+ *   - Every call uses the same array, so calls whose GPU work overlaps (different streams,
+ *     or different threads on one device) race and corrupt each other's result; order
+ *     them on one stream.  The scratch contents left by a call are cleared by the next.
+ * Synchronises. */
+amg_status cwm_suitor_match_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr,
+                                   const int32_t *d_col, const double *d_w, int32_t *d_mate,
+                                   void *stream);
+
 /* Pairwise aggregation (Sec. 2.2, Algorithm 2, ids ascending by smallest member) and the
  * prolongator by orthonormal projection of v (Sec. 2.2):
  *   d_agg (n int32): aggregate of each vertex;  d_p (n doubles): the one entry of each

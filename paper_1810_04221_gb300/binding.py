@@ -25,6 +25,7 @@ EXPORTS = (
     "amg_num_levels", "amg_level_info", "amg_level_export", "amg_sweep_mate", "cwm_edge_weights",
     "cwm_suitor_match", "cwm_aggregate", "cwm_galerkin", "amg_status_string", "amg_last_error",
     "amg_trace_enable", "amg_trace_reset", "amg_trace_count", "amg_trace_get", "amg_launch_count",
+    "cwm_suitor_match_noalloc",
 )
 
 
@@ -100,6 +101,7 @@ def load(path: str | None = None):
             "amg_sweep_mate": (i, [vp, i, i, vp, ip, vp]),
             "cwm_edge_weights": (i, [i, i64, vp, vp, vp, vp, vp, vp]),
             "cwm_suitor_match": (i, [i, i64, vp, vp, vp, vp, vp]),
+            "cwm_suitor_match_noalloc": (i, [i, i64, vp, vp, vp, vp, vp]),
             "cwm_aggregate": (i, [i, vp, vp, vp, vp, vp, ip, ip, vp]),
             "cwm_galerkin": (i, [i, vp, vp, vp, i, vp, vp, vp, vp, vp, i64, C.POINTER(i64), vp]),
             "amg_trace_enable": (i, [vp, i, C.c_char_p]),
@@ -268,6 +270,15 @@ def cwm_suitor_match(row_ptr, col, w, mate=None, stream=None):
     _check(load().cwm_suitor_match(n, nnz, _dev(row_ptr, torch.int32, "row_ptr"), _dev(col, torch.int32, "col"),
                                    _dev(w, torch.float64, "w", nnz), _dev(mate, torch.int32, "mate", n),
                                    _stream(stream)), "cwm_suitor_match")
+    return mate
+
+
+def cwm_suitor_match_noalloc(row_ptr, col, w, mate, stream=None):
+    """cwm_suitor_match without any device allocation: `mate` must be given (n int32)."""
+    n, nnz = row_ptr.numel() - 1, col.numel()
+    _check(load().cwm_suitor_match_noalloc(n, nnz, _dev(row_ptr, torch.int32, "row_ptr"), _dev(col, torch.int32, "col"),
+                                           _dev(w, torch.float64, "w", nnz), _dev(mate, torch.int32, "mate", n),
+                                           _stream(stream)), "cwm_suitor_match_noalloc")
     return mate
 
 
