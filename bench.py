@@ -110,6 +110,8 @@ class Clocks:
         self.gpu = gpu_index
 
     def start(self):
+        if self.gpu < 0:
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -204,7 +206,7 @@ def run_cuda(args, rank, world, dist):
     torch.cuda.synchronize()
 
     # timed region: K steps, device events on the launching stream, dominant class traced
-    clocks = Clocks(local)
+    clocks = Clocks(local) if not args.profile else Clocks(-1)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     traces, infos, statuses = [], [], []
     if dist is not None:
@@ -234,6 +236,11 @@ def run_cuda(args, rank, world, dist):
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
+
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": round(ms_per_step, 3), "dominant": dominant}))
+        return
 
     # e2e through the C ABI with host buffers (pinned), copies inside the timed region
     h_rp, h_ci, h_val, h_v, h_b = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (rp, ci, val, v, b))
@@ -385,6 +392,8 @@ def main():
     ap.add_argument("--itmax", type=int, default=5000)
     ap.add_argument("--variant", type=int, default=1, help="also time the other V-cycle precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed steps only (no e2e, variant, CPU baseline): for ncu launch lists")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "cuda" else args.warmup
 

@@ -35,6 +35,9 @@ struct Level {
   // V-cycle work vectors
   DBuf<double> b, x, t1, t2;
   DBuf<float> b32, x32, t132, t232;
+  // coarsest level only: the dense operator of the coarse sweeps (n <= kDenseCoarseMax)
+  DBuf<double> xdense;
+  DBuf<float> xdense32;
 
   CsrView<double> view64() const {
     CsrView<double> a;
@@ -87,6 +90,7 @@ struct amg_hierarchy {
   Mailbox box;
   // FCG vectors and reductions
   DBuf<double> r, w, d, vv, q, part, part2, scal;
+  DBuf<unsigned> tick;  // last-block tickets of the fused reductions (kept at zero between launches)
   double t_setup_ms = 0.0, t_solve_ms = 0.0;
   Tracer trace;
 };
@@ -139,10 +143,11 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   // scratch sized for the largest (first) sweep
   const int nf = F.n;
   const long long nnzf = F.nnz;
-  DBuf<double> w;
+  DBuf<double> w, dv;
   DBuf<unsigned char> skeys;
   DBuf<int> mate, m1, m2, ids, scan, cnt, longr, misc;
   CWM_TRY(w.alloc(nnzf, s));
+  CWM_TRY(dv.alloc(nf, s));
   CWM_TRY(skeys.alloc(suitor_scratch_bytes(nf), s));
   CWM_TRY(mate.alloc(nf, s));
   CWM_TRY(m1.alloc(nf, s));
@@ -164,7 +169,7 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   F.sweep_mate.clear();
 
   for (int sweep = 0; sweep < S; ++sweep) {
-    CWM_TRY(edge_weights(cn, cnnz, crp, cci, cval, cdiag, cv, w.get(), s));
+    CWM_TRY(edge_weights(cn, cnnz, crp, cci, cval, cdiag, cv, w.get(), dv.get(), s));
     CWM_TRY(suitor_match(cn, cnnz, crp, cci, w.get(), skeys.get(), mate.get(),
                          default_cap(h->prm, cn, cnnz), h->err.get(), s));
     SweepOut o;
@@ -190,7 +195,6 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
     CWM_TRY(o.ci.alloc(cnnz, s));
     CWM_TRY(o.val.alloc(cnnz, s));
     CWM_TRY(o.diag.alloc(nc, s));
-    CWM_TRY(o.dl1.alloc(nc, s));
     GalerkinWork gw;
     gw.cnt = cnt.get();
     gw.long_rows = longr.get();
@@ -201,7 +205,7 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
     CWM_TRY(galerkin_count(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(), gw,
                            h->err.get(), s));
     CWM_TRY(galerkin_fill(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(),
-                          o.ci.get(), o.val.get(), o.diag.get(), o.dl1.get(), gw, h->err.get(), s));
+                          o.ci.get(), o.val.get(), o.diag.get(), nullptr, gw, h->err.get(), s));
     CWM_CUDA(cudaMemcpyAsync(h->box.ints + 4, o.rp.get() + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
     CWM_TRY(read_err(h, "amg_setup (Galerkin)"));
     o.nnz = h->box.ints[4];
@@ -244,7 +248,8 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   C.val = std::move(last.val);
   C.v = std::move(last.v);
   C.diag = std::move(last.diag);
-  C.dl1 = std::move(last.dl1);
+  CWM_TRY(C.dl1.alloc(C.n, s));
+  CWM_TRY(l1_norms(C.view64(), C.dl1.get(), s));
   h->lev.push_back(std::move(C));
   *made = (int)sw.size() == S;  // a sweep without pairs ends the hierarchy after this level
   return AMG_OK;
@@ -287,6 +292,7 @@ struct LevelVec<double> {
   static double *x(Level &L) { return L.x.get(); }
   static double *t1(Level &L) { return L.t1.get(); }
   static double *t2(Level &L) { return L.t2.get(); }
+  static const double *dense(const Level &L) { return L.xdense.get(); }
 };
 template <>
 struct LevelVec<float> {
@@ -297,6 +303,7 @@ struct LevelVec<float> {
   static float *x(Level &L) { return L.x32.get(); }
   static float *t1(Level &L) { return L.t132.get(); }
   static float *t2(Level &L) { return L.t232.get(); }
+  static const float *dense(const Level &L) { return L.xdense32.get(); }
 };
 
 // x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
@@ -312,6 +319,7 @@ amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
   const int nl = (int)h->lev.size();
   if (k == nl - 1) {  // coarsest: l1-Jacobi sweeps from zero
     const int sweeps = h->prm.coarse_sweeps;
+    if (LV::dense(L)) return dense_coarse_apply<V>(A.n, LV::dense(L), b, x, s);
     if (A.n <= kCoarseBlockMax) return coarse_solve_block<V>(A, dinv, b, x, sweeps, s);
     if (sweeps <= 0) { CWM_CUDA(cudaMemsetAsync(x, 0, sizeof(V) * (size_t)A.n, s)); return AMG_OK; }
     const V *cur = nullptr;
@@ -332,7 +340,8 @@ amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
     xs = dst;
   }
   Level &C = h->lev[k + 1];
-  CWM_TRY(resid_restrict<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, LV::b(C), s));
+  V *rtmp = (xs == t1) ? t2 : t1;  // free until the prolongation writes it
+  CWM_TRY(resid_restrict_rb<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, rtmp, LV::b(C), s));
   CWM_TRY(vcycle_level<V>(h, k + 1, LV::b(C), LV::x(C)));
   V *y = (xs == t1) ? t2 : t1;
   CWM_TRY(prolong<V>(A.n, L.agg.get(), LV::p(L), LV::x(C), xs, y, s));
@@ -460,6 +469,21 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   }
   for (Level &L : h->lev) CWM_TRY(finish_level(h, L));
   h->lev.back().nsweeps = 0;
+  {
+    Level &Lc = h->lev.back();
+    LevelTag tag((int)h->lev.size() - 1);
+    if (Lc.n <= kDenseCoarseMax) {
+      const size_t nn = (size_t)Lc.n * Lc.n;
+      DBuf<double> tmp;
+      CWM_TRY(Lc.xdense.alloc(nn, s));
+      CWM_TRY(tmp.alloc(nn, s));
+      CWM_TRY(dense_coarse_build(Lc.view64(), Lc.dinv.get(), P.coarse_sweeps, Lc.xdense.get(), tmp.get(), s));
+      if (P.vcycle_fp32) {
+        CWM_TRY(Lc.xdense32.alloc(nn, s));
+        CWM_TRY(to_float((long long)nn, Lc.xdense.get(), Lc.xdense32.get(), s));
+      }
+    }
+  }
 
   // FCG work vectors
   CWM_TRY(h->r.alloc(n, s));
@@ -471,6 +495,8 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   CWM_TRY(h->part.alloc(3 * (size_t)nb, s));
   CWM_TRY(h->part2.alloc(nb, s));
   CWM_TRY(h->scal.alloc(kFcgSlots, s));
+  CWM_TRY(h->tick.alloc(4, s));
+  CWM_CUDA(cudaMemsetAsync(h->tick.get(), 0, 4 * sizeof(unsigned), s));
   CWM_CUDA(cudaStreamSynchronize(s));
   return AMG_OK;
 }
@@ -641,11 +667,10 @@ amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rt
   while (status != AMG_OK && it < itmax) {
     const int first = it == 0;
     CWM_TRY(apply_vcycle(h, h->r.get(), h->w.get()));
-    CWM_TRY(spmv_dots(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(), s));
-    CWM_TRY(fcg_scalars(nb, h->part.get(), scal, first, s));
+    CWM_TRY(spmv_dots_scalars(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
+                              scal, h->tick.get(), first, s));
     CWM_TRY(fcg_update(n, h->w.get(), h->vv.get(), h->d.get(), h->q.get(), d_x, h->r.get(), scal, h->part2.get(),
-                       first, s));
-    CWM_TRY(reduce_into(nb, h->part2.get(), scal, kRR, s));
+                       h->tick.get() + 1, first, s));
     CWM_CUDA(cudaMemcpyAsync(h->box.dbls, scal, sizeof(double) * kFcgSlots, cudaMemcpyDeviceToHost, s));
     CWM_CUDA(cudaStreamSynchronize(s));
     if (h->box.dbls[kFlags] != 0.0) {
@@ -730,14 +755,15 @@ amg_status cwm_edge_weights(int n, int64_t nnz, const int32_t *d_row_ptr, const 
   }
   if (n == 0) return AMG_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  DBuf<double> diag;
+  DBuf<double> diag, dv;
   DBuf<int> err;
   int h_err = 0;
   CWM_TRY(diag.alloc(n, s));
+  CWM_TRY(dv.alloc(n, s));
   CWM_TRY(err.alloc(1, s));
   CWM_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
   CWM_TRY(extract_diag(n, d_row_ptr, d_col, d_val, diag.get(), err.get(), s));
-  CWM_TRY(edge_weights(n, nnz, d_row_ptr, d_col, d_val, diag.get(), d_v, d_w, s));
+  CWM_TRY(edge_weights(n, nnz, d_row_ptr, d_col, d_val, diag.get(), d_v, d_w, dv.get(), s));
   return read_bits(err.get(), &h_err, s, "cwm_edge_weights");
 }
 

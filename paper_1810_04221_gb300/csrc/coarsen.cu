@@ -116,19 +116,89 @@ __global__ void __launch_bounds__(256) k_edge_weights(int n, const int *__restri
   }
 }
 
-amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
-                        const double *diag, const double *v, double *w, cudaStream_t s) {
-  // rp, ci, val, w written; v and diag of each row (gathers of neighbours counted once)
-  CWM_TRACE("weights", 4.0 * (n + 1) + 20.0 * nnz + 16.0 * n, s);
-  const int T = tile_for_mean(n ? (double)nnz / n : 1.0);
-  const int block = 256;
-  const int grid = grid_for((long long)n * T, block, num_sms() * 16);
-  switch (T) {
-    case 4: k_edge_weights<4><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
-    case 8: k_edge_weights<8><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
-    case 16: k_edge_weights<16><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
-    default: k_edge_weights<32><<<grid, block, 0, s>>>(n, rp, ci, val, diag, v, w); break;
+// Row-block form of the same computation: a block of kWB threads owns kWB consecutive
+// rows and streams their slots in chunks of kWB * kWE with coalesced loads; each slot's
+// row comes from a shared-memory row-id map filled by the row's thread.
+constexpr int kWB = 256;
+constexpr int kWE = 8;
+constexpr int kWC = kWB * kWE;
+
+// dv[i] = (a_ii v_i) v_i: the per-vertex half of the denominator, rounded exactly as in
+// the per-slot expression, so that den = dv[a] + dv[b] is bit-identical.
+__global__ void k_vertex_dv(int n, const double *__restrict__ diag, const double *__restrict__ v,
+                            double *__restrict__ dv) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dv[i] = __dmul_rn(__dmul_rn(diag[i], v[i]), v[i]);
+}
+
+__global__ void __launch_bounds__(kWB) k_edge_weights_rb(int n, const int *__restrict__ rp,
+                                                         const int *__restrict__ ci,
+                                                         const double *__restrict__ val,
+                                                         const double *__restrict__ diag,
+                                                         const double *__restrict__ v,
+                                                         double *__restrict__ w) {
+  // `diag` holds dv = (a_ii v_i) v_i here (see k_vertex_dv)
+  __shared__ int s_rp[kWB + 1];
+  __shared__ double s_v[kWB], s_d[kWB];
+  __shared__ unsigned char s_row[kWC];
+  const int t = threadIdx.x;
+  const int r0 = blockIdx.x * kWB;
+  const int nrows = min(kWB, n - r0);
+  for (int i = t; i <= nrows; i += kWB) s_rp[i] = rp[r0 + i];
+  if (t < nrows) {
+    s_v[t] = v[r0 + t];
+    s_d[t] = diag[r0 + t];
   }
+  __syncthreads();
+  const int rs = s_rp[0], re = s_rp[nrows];
+  const int my_s = t < nrows ? s_rp[t] : 0, my_e = t < nrows ? s_rp[t + 1] : 0;
+  for (int c0 = rs; c0 < re; c0 += kWC) {
+    const int cend = min(c0 + kWC, re);
+    for (int k = max(my_s, c0); k < min(my_e, cend); ++k) s_row[k - c0] = (unsigned char)t;
+    __syncthreads();
+    int col[kWE];
+    double a[kWE];
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      const int k = c0 + e * kWB + t;
+      const bool in = k < cend;
+      col[e] = in ? __ldcs(ci + k) : -1;
+      a[e] = in ? __ldcs(val + k) : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      if (col[e] < 0) continue;
+      const int k = c0 + e * kWB + t;
+      const int il = s_row[k - c0];
+      const int i = r0 + il, j = col[e];
+      double c = 0.0;
+      if (j != i && a[e] != 0.0) {
+        const double vi = s_v[il], di = s_d[il];
+        const double vj = __ldg(v + j), dj = __ldg(diag + j);
+        const bool lo_i = i < j;
+        const double va = lo_i ? vi : vj, vb = lo_i ? vj : vi;
+        const double da = lo_i ? di : dj, db = lo_i ? dj : di;
+        const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a[e]), va), vb);
+        const double den = __dadd_rn(da, db);
+        if (den != 0.0) {
+          const double cc = __dsub_rn(1.0, __ddiv_rn(num, den));
+          if (cc > 0.0) c = cc;
+        }
+      }
+      __stcs(w + k, c);
+    }
+    __syncthreads();
+  }
+}
+
+amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
+                        const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  // rp, ci, val, w written; v and diag of each row (gathers of neighbours counted once)
+  CWM_TRACE("weights", 4.0 * (n + 1) + 20.0 * nnz + 32.0 * n, s);
+  k_vertex_dv<<<grid_for(n, 256, num_sms() * 8), 256, 0, s>>>(n, diag, v, dv_scratch);
+  CWM_LAUNCH();
+  k_edge_weights_rb<<<(n + kWB - 1) / kWB, kWB, 0, s>>>(n, rp, ci, val, dv_scratch, v, w);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -249,7 +319,8 @@ amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, cons
   k_clear_keys<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, S);
   CWM_LAUNCH();
   if (cap <= 0) cap = nnz + (long long)n + 1024;
-  const int T = tile_for_mean(n ? (double)nnz / n : 1.0);
+  const double mean = n ? (double)nnz / n : 1.0;
+  const int T = tile_for_mean(mean);
   const int block = 256;
   const int grid = grid_for((long long)n * T, block, num_sms() * 8);
   switch (T) {

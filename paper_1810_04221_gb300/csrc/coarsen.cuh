@@ -18,8 +18,9 @@ amg_status check_input(int n, long long nnz, const int *rp, const int *ci, const
                        bool check_sym, int *d_err, cudaStream_t s);
 amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, double *diag,
                         int *d_err, cudaStream_t s);
+// dv_scratch: n doubles (per-vertex (a_ii v_i) v_i)
 amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
-                        const double *diag, const double *v, double *w, cudaStream_t s);
+                        const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s);
 size_t suitor_scratch_bytes(int n);
 amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, const double *w,
                         void *scratch, int *mate, long long cap, int *d_err, cudaStream_t s);

@@ -103,9 +103,158 @@ __device__ __forceinline__ int next_pow2(int x) {
   return p;
 }
 
+// ------------------------------------------------------------ register rows ----
+// A coarse row with L <= G entries held one per lane by a group of G lanes (G = 16 or 32,
+// gmask = the group's lanes).  Lanes with equal J are found with __match_any_sync, so no
+// sort is needed: the lowest lane of each equal-J group leads it, counts it, and in the
+// fill pass gathers the group's (at most four) terms with shuffles, orders them by
+// (min(i,j), max(i,j), i), sums them from +0.0, and writes at its rank among the leaders.
+template <bool FILL>
+__device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigned gmask, int gbase, int glen,
+                                                 const int *__restrict__ ci, const double *__restrict__ val,
+                                                 const int *__restrict__ agg, const double *__restrict__ p,
+                                                 int *__restrict__ cnt, const int *__restrict__ rpc,
+                                                 int *__restrict__ cic, double *__restrict__ valc,
+                                                 double *__restrict__ diag_c, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane - gbase;
+  const int L = r.L1 + r.L2;
+  const bool act = gl < L;
+  int k = 0, i = 0, j = 0;
+  unsigned J = 0x80000000u | (unsigned)lane;  // unique per lane, never a real column
+  if (act) {
+    const bool first = gl < r.L1;
+    i = first ? r.i1 : r.i2;
+    k = first ? r.s1 + gl : r.s2 + (gl - r.L1);
+    j = ci[k];
+    J = (unsigned)agg[j];
+  }
+  const unsigned mm = __match_any_sync(gmask, J);
+  const bool leader = act && lane == __ffs(mm) - 1;
+  const unsigned lead = __ballot_sync(gmask, leader) & gmask;
+  if (!FILL) {
+    if (gl == 0) cnt[I] = __popc(lead);
+    return;
+  }
+  double t = 0.0;
+  int kmin = 0, kmax = 0;
+  if (act) {
+    t = __dmul_rn(__dmul_rn(p[i], p[j]), val[k]);
+    kmin = min(i, j);
+    kmax = max(i, j);
+  }
+  const int members = __popc(mm);
+  int src[4];
+  unsigned rest = mm;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    src[m] = rest ? __ffs(rest) - 1 : lane;
+    rest &= rest - 1u;
+  }
+  double tm[4];
+  int kmn[4], kmx[4], im[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    tm[m] = __shfl_sync(gmask, t, src[m]);
+    kmn[m] = __shfl_sync(gmask, kmin, src[m]);
+    kmx[m] = __shfl_sync(gmask, kmax, src[m]);
+    im[m] = __shfl_sync(gmask, i, src[m]);
+  }
+  int rank = 0;
+  for (int l = gbase; l < gbase + glen; ++l) {
+    const unsigned Jl = __shfl_sync(gmask, J, l);
+    if (((lead >> l) & 1u) && Jl < J) ++rank;
+  }
+  if (!leader) return;
+  if (members > 4) atomicOr(err, kErrInvalid);
+  const int len = members < 4 ? members : 4;
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    if (m >= len) { kmn[m] = kmx[m] = im[m] = INT_MAX; tm[m] = 0.0; }
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+#pragma unroll
+    for (int b = a; b > 0; --b) {
+      const bool swap = kmn[b] < kmn[b - 1] ||
+                        (kmn[b] == kmn[b - 1] && (kmx[b] < kmx[b - 1] || (kmx[b] == kmx[b - 1] && im[b] < im[b - 1])));
+      if (swap) {
+        int x;
+        double y;
+        x = kmn[b]; kmn[b] = kmn[b - 1]; kmn[b - 1] = x;
+        x = kmx[b]; kmx[b] = kmx[b - 1]; kmx[b - 1] = x;
+        x = im[b]; im[b] = im[b - 1]; im[b - 1] = x;
+        y = tm[b]; tm[b] = tm[b - 1]; tm[b - 1] = y;
+      }
+    }
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    if (m < len) sum = __dadd_rn(sum, tm[m]);
+  const int out = rpc[I] + rank;
+  cic[out] = (int)J;
+  valc[out] = sum;
+  if ((int)J == I && diag_c) diag_c[I] = sum;
+}
+
+// ------------------------------------------------------------ shared-memory rows ----
+// A coarse row with 32 < L <= kWarpCap entries: keys (J, slot) sorted in shared memory by
+// the warp (bitonic), runs of equal J summed in canonical order.
+template <bool FILL>
+__device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsigned long long *keys,
+                                                  const int *__restrict__ ci, const double *__restrict__ val,
+                                                  const int *__restrict__ agg, const double *__restrict__ p,
+                                                  int *__restrict__ cnt, const int *__restrict__ rpc,
+                                                  int *__restrict__ cic, double *__restrict__ valc,
+                                                  double *__restrict__ diag_c, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int L = r.L1 + r.L2;
+  const int P = next_pow2(L < 32 ? 32 : L);
+  for (int q = lane; q < P; q += 32) keys[q] = q < L ? make_key(r, q, ci, agg) : ~0ull;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int q = lane; q < P; q += 32) {
+        const int l = q ^ j;
+        if (l > q) {
+          const unsigned long long a = keys[q], b = keys[l];
+          if ((a > b) == ((q & k) == 0)) { keys[q] = b; keys[l] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  int base = 0;
+  for (int q0 = 0; q0 < L; q0 += 32) {
+    const int q = q0 + lane;
+    bool head = false;
+    unsigned J = 0;
+    if (q < L) {
+      J = (unsigned)(keys[q] >> 32);
+      head = q == 0 || (unsigned)(keys[q - 1] >> 32) != J;
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, head);
+    if (FILL && head) {
+      int len = 1;
+      while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
+      if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
+      const double s = run_value(r, keys, q, len, ci, val, p);
+      const int out = rpc[I] + base + __popc(ball & ((1u << lane) - 1u));
+      cic[out] = (int)J;
+      valc[out] = s;
+      if ((int)J == I && diag_c) diag_c[I] = s;
+    }
+    base += __popc(ball);
+  }
+  if (!FILL && lane == 0) cnt[I] = base;
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ warp kernel ----
-// FILL = false: cnt[I] = number of distinct J; long rows are queued.
-// FILL = true:  writes columns and values at rpc[I]; diag_c / dl1_c when given.
+// Each warp takes two consecutive coarse rows.  When both gather <= 16 entries each half
+// warp handles one in registers; otherwise the warp handles them in turn (registers up to
+// 32 entries, shared memory up to kWarpCap, longer rows queued for the block kernel).
+// FILL = false: cnt[I] = number of distinct J.  FILL = true: columns and values at rpc[I].
 template <bool FILL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_galerkin_warp(int nc, const int *__restrict__ rp, const int *__restrict__ ci,
@@ -113,69 +262,43 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                     const int *__restrict__ m2, const int *__restrict__ agg,
                     const double *__restrict__ p, int *__restrict__ cnt,
                     const int *__restrict__ rpc, int *__restrict__ cic, double *__restrict__ valc,
-                    double *__restrict__ diag_c, double *__restrict__ dl1_c,
-                    int *__restrict__ long_rows, int *__restrict__ n_long, int *err) {
+                    double *__restrict__ diag_c, int *__restrict__ long_rows, int *__restrict__ n_long, int *err) {
   __shared__ unsigned long long sbuf[kWarpsPerBlock][kWarpCap];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  unsigned long long *keys = sbuf[wib];
+  const int half = lane >> 4;
+  unsigned long long *keys = sbuf[threadIdx.x >> 5];
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long row = warp0; row < nc; row += nwarps) {
-    const int I = (int)row;
-    const RowSrc r = row_src(I, m1, m2, rp);
-    const int L = r.L1 + r.L2;
-    if (L > kWarpCap) {
-      if (!FILL && lane == 0) long_rows[atomicAdd(n_long, 1)] = I;
+  for (long long base = warp0 * 2; base < nc; base += nwarps * 2) {
+    const int Ih = (int)(base + half);
+    RowSrc rh{};
+    int Lh = 0;
+    if (Ih < nc) {
+      rh = row_src(Ih, m1, m2, rp);
+      Lh = rh.L1 + rh.L2;
+    }
+    const int L0 = __shfl_sync(0xffffffffu, Lh, 0), L1 = __shfl_sync(0xffffffffu, Lh, 16);
+    if (L0 <= 16 && L1 <= 16) {
+      if (Ih < nc)
+        galerkin_row_reg<FILL>(rh, Ih, half ? 0xffff0000u : 0x0000ffffu, half * 16, 16, ci, val, agg, p, cnt, rpc,
+                               cic, valc, diag_c, err);
+      __syncwarp();
       continue;
     }
-    const int P = next_pow2(L < 32 ? 32 : L);
-    for (int q = lane; q < P; q += 32) keys[q] = q < L ? make_key(r, q, ci, agg) : ~0ull;
-    __syncwarp();
-    for (int k = 2; k <= P; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int q = lane; q < P; q += 32) {
-          const int l = q ^ j;
-          if (l > q) {
-            const unsigned long long a = keys[q], b = keys[l];
-            if ((a > b) == ((q & k) == 0)) { keys[q] = b; keys[l] = a; }
-          }
-        }
-        __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+      const int I = (int)base + h;
+      if (I >= nc) break;
+      const RowSrc r = row_src(I, m1, m2, rp);
+      const int L = r.L1 + r.L2;
+      if (L <= 32) {
+        galerkin_row_reg<FILL>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+      } else if (L <= kWarpCap) {
+        galerkin_row_smem<FILL>(r, I, keys, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+      } else if (!FILL && lane == 0) {
+        long_rows[atomicAdd(n_long, 1)] = I;
       }
+      __syncwarp();
     }
-    int base = 0;
-    double l1 = 0.0;
-    for (int q0 = 0; q0 < L; q0 += 32) {
-      const int q = q0 + lane;
-      bool head = false;
-      unsigned J = 0;
-      if (q < L) {
-        J = (unsigned)(keys[q] >> 32);
-        head = q == 0 || (unsigned)(keys[q - 1] >> 32) != J;
-      }
-      const unsigned ball = __ballot_sync(0xffffffffu, head);
-      if (FILL && head) {
-        int len = 1;
-        while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
-        if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
-        const double s = run_value(r, keys, q, len, ci, val, p);
-        const int out = rpc[I] + base + __popc(ball & ((1u << lane) - 1u));
-        cic[out] = (int)J;
-        valc[out] = s;
-        if ((int)J == I && diag_c) diag_c[I] = s;
-        l1 += fabs(s);
-      }
-      base += __popc(ball);
-    }
-    if (!FILL) {
-      if (lane == 0) cnt[I] = base;
-    } else if (dl1_c) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-      if (lane == 0) dl1_c[I] = l1;
-    }
-    __syncwarp();
   }
 }
 
@@ -295,11 +418,10 @@ amg_status galerkin_count(const int *rp, const int *ci, const double *val, int n
   // members and row bounds, ci and agg(ci) of both member rows, counts, scan
   CWM_TRACE("galerkin_count", 4.0 * work.nnz_fine + 4.0 * work.n_fine + 40.0 * nc, s);
   const int block = kWarpsPerBlock * 32;
-  const int grid = grid_for((long long)nc * 32, block, num_sms() * 8);
+  const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
   CWM_CUDA(cudaMemsetAsync(work.n_long, 0, sizeof(int), s));
   k_galerkin_warp<false><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, nullptr,
-                                                nullptr, nullptr, nullptr, nullptr, work.long_rows,
-                                                work.n_long, d_err);
+                                                nullptr, nullptr, nullptr, work.long_rows, work.n_long, d_err);
   CWM_LAUNCH();
   k_galerkin_block<false><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
       rp, ci, val, m1, m2, agg, p, work.cnt, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -317,9 +439,9 @@ amg_status galerkin_fill(const int *rp, const int *ci, const double *val, int nc
   // reads as in the count pass plus val and p; writes of A_c not included (size unknown here)
   CWM_TRACE("galerkin_fill", 12.0 * work.nnz_fine + 12.0 * work.n_fine + 44.0 * nc, s);
   const int block = kWarpsPerBlock * 32;
-  const int grid = grid_for((long long)nc * 32, block, num_sms() * 8);
+  const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
   k_galerkin_warp<true><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic,
-                                               valc, diag_c, dl1_c, nullptr, nullptr, d_err);
+                                               valc, diag_c, nullptr, nullptr, d_err);
   CWM_LAUNCH();
   k_galerkin_block<true><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
       rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic, valc, diag_c, dl1_c, work.long_rows,

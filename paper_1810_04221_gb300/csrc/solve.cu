@@ -60,6 +60,105 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
+// ------------------------------------------------------------ row blocks ----
+// A block of kRB threads owns kRB consecutive rows (thread t <-> row r0 + t).  The block's
+// entries [rp[r0], rp[r0 + kRB]) are staged in chunks of kRB * kRBE: every thread issues
+// kRBE coalesced loads of col and val (streaming cache hint) into shared memory, then each
+// thread walks its own row's slice in ascending order, gathering x and accumulating with
+// one fused multiply-add per entry.  One FMA per nonzero matters on GB300, whose FP64 pipe
+// retires about 500 G instructions/s (a DMUL + DADD pair per nonzero would make the FP64
+// SpMV compute-bound).
+constexpr int kRB = 256;
+constexpr int kRBE = 8;
+constexpr int kRBC = kRB * kRBE;
+
+template <class V>
+struct RowBlockSmem {
+  V val[kRBC];
+  int col[kRBC];
+  int rp[kRB + 1];
+};
+
+// Stages the row pointers of rows [r0, r0 + nrows] (all threads call it).
+__device__ __forceinline__ void rb_stage_rp(const int *__restrict__ rp, int r0, int nrows, int *s_rp) {
+  for (int i = threadIdx.x; i <= nrows; i += kRB) s_rp[i] = rp[r0 + i];
+  __syncthreads();
+}
+
+// Row dot of row r0 + threadIdx.x with x (0 for threads beyond nrows); ABS = sum of |a_ij|.
+template <class V, bool ABS>
+__device__ __forceinline__ V rb_row_dot(const int *__restrict__ ci, const V *__restrict__ val,
+                                        const V *__restrict__ x, int nrows, RowBlockSmem<V> &sm) {
+  const int t = threadIdx.x;
+  const int rs = sm.rp[0], re = sm.rp[nrows];
+  const int my_s = t < nrows ? sm.rp[t] : 0, my_e = t < nrows ? sm.rp[t + 1] : 0;
+  V acc = V(0);
+  for (int c0 = rs; c0 < re; c0 += kRBC) {
+    const int cend = min(c0 + kRBC, re);
+    int col[kRBE];
+    V a[kRBE];
+#pragma unroll
+    for (int e = 0; e < kRBE; ++e) {
+      const int k = c0 + e * kRB + t;
+      const bool in = k < cend;
+      col[e] = (in && !ABS) ? __ldcs(ci + k) : 0;
+      a[e] = in ? __ldcs(val + k) : V(0);
+    }
+#pragma unroll
+    for (int e = 0; e < kRBE; ++e) {
+      sm.val[e * kRB + t] = a[e];
+      if (!ABS) sm.col[e * kRB + t] = col[e];
+    }
+    __syncthreads();
+    const int lo = max(my_s, c0) - c0, hi = min(my_e, cend) - c0;
+    int k = lo;
+    if (ABS) {
+      for (; k < hi; ++k) acc += fabs(sm.val[k]);
+    } else {
+      // four independent gathers in flight, then the FMAs in order
+      for (; k + 4 <= hi; k += 4) {
+        const V x0 = __ldg(x + sm.col[k]), x1 = __ldg(x + sm.col[k + 1]);
+        const V x2 = __ldg(x + sm.col[k + 2]), x3 = __ldg(x + sm.col[k + 3]);
+        acc = fma(sm.val[k], x0, acc);
+        acc = fma(sm.val[k + 1], x1, acc);
+        acc = fma(sm.val[k + 2], x2, acc);
+        acc = fma(sm.val[k + 3], x3, acc);
+      }
+      for (; k < hi; ++k) acc = fma(sm.val[k], __ldg(x + sm.col[k]), acc);
+    }
+    __syncthreads();
+  }
+  return acc;
+}
+
+static int rb_grid(long long n) { return (int)((n + kRB - 1) / kRB); }
+
+// Block sums of up to three values per thread with few FP64 instructions (blockDim ==
+// kRB): the values go to shared memory, then warp w folds value w (kRB/32 sequential adds
+// per lane and five shuffle steps).  GB300 retires FP64 adds as whole-warp instructions at
+// a low rate, so this beats a shuffle tree in every warp.  Results valid in every thread.
+template <int NV>
+__device__ __forceinline__ void block_sums(const double (&in)[NV], double (&out)[NV]) {
+  __shared__ double s_in[NV][kRB];
+  __shared__ double s_out[NV];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) s_in[v][threadIdx.x] = in[v];
+  __syncthreads();
+  if (w < NV) {
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < kRB / 32; ++k) a += s_in[w][lane * (kRB / 32) + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) s_out[w] = a;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = s_out[v];
+  __syncthreads();
+}
+
 // ------------------------------------------------------------ elementwise ----
 template <class V>
 __global__ void k_scale(int n, const V *__restrict__ dinv, const V *__restrict__ b, V *__restrict__ y) {
@@ -109,10 +208,24 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
 }
 
 template <class V>
+__global__ void __launch_bounds__(kRB) k_jacobi_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                   const V *__restrict__ val, const V *__restrict__ dinv,
+                                                   const V *__restrict__ b, const V *__restrict__ x,
+                                                   V *__restrict__ y) {
+  __shared__ RowBlockSmem<V> sm;
+  const int r0 = blockIdx.x * kRB;
+  const int nrows = min(kRB, n - r0);
+  rb_stage_rp(rp, r0, nrows, sm.rp);
+  const V dot = rb_row_dot<V, false>(ci, val, x, nrows, sm);
+  const int r = r0 + threadIdx.x;
+  if (threadIdx.x < nrows) y[r] = x[r] + dinv[r] * (b[r] - dot);
+}
+
+template <class V>
 amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V *y, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("jacobi", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 4.0 * sizeof(V) * A.n, s);
-  CWM_DISPATCH_T(A.tile, (k_jacobi<V, kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, y)));
+  k_jacobi_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, y);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -143,6 +256,50 @@ __global__ void __launch_bounds__(kBlock)
     }
     if (active && lane == 0) bc[I] = acc;
   }
+}
+
+// r = b - A x (x may be NULL: r = b), row blocks
+template <class V>
+__global__ void __launch_bounds__(kRB) k_resid_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                  const V *__restrict__ val, const V *__restrict__ b,
+                                                  const V *__restrict__ x, V *__restrict__ r) {
+  __shared__ RowBlockSmem<V> sm;
+  const int r0 = blockIdx.x * kRB;
+  const int nrows = min(kRB, n - r0);
+  rb_stage_rp(rp, r0, nrows, sm.rp);
+  const V dot = x ? rb_row_dot<V, false>(ci, val, x, nrows, sm) : V(0);
+  const int i = r0 + threadIdx.x;
+  if (threadIdx.x < nrows) r[i] = b[i] - dot;
+}
+
+// bc[I] = sum over the members m of I (ascending) of p_m r_m
+template <class V>
+__global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__restrict__ mlist,
+                           const V *__restrict__ p, const V *__restrict__ r, V *__restrict__ bc) {
+  for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += (long long)gridDim.x * blockDim.x) {
+    const int s = mptr[I], e = mptr[I + 1];
+    V acc = V(0);
+    for (int k = s; k < e; ++k) {
+      const int m = mlist[k];
+      acc += p[m] * r[m];
+    }
+    bc[I] = acc;
+  }
+}
+
+template <class V>
+amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
+                             const V *b, const V *x, V *r_scratch, V *bc, cudaStream_t s) {
+  if (nc == 0) return AMG_OK;
+  {
+    CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
+    k_resid_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r_scratch);
+    CWM_LAUNCH();
+  }
+  CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
+  k_restrict<V><<<grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s>>>(nc, mptr, mlist, p, r_scratch, bc);
+  CWM_LAUNCH();
+  return AMG_OK;
 }
 
 template <class V>
@@ -180,6 +337,49 @@ __global__ void __launch_bounds__(1024) k_coarse_block(int n, const int *__restr
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xa[i];
 }
 
+// The whole coarsest system staged in shared memory (matrix, D^{-1}, b, two x copies).
+template <class V>
+__global__ void __launch_bounds__(1024) k_coarse_smem(int n, int nnz, const int *__restrict__ rp,
+                                                      const int *__restrict__ ci, const V *__restrict__ val,
+                                                      const V *__restrict__ dinv, const V *__restrict__ b,
+                                                      V *__restrict__ x, int sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *s_val = reinterpret_cast<V *>(smem_raw);
+  V *s_dinv = s_val + nnz;
+  V *s_b = s_dinv + n;
+  V *xa = s_b + n;
+  V *xb = xa + n;
+  int *s_rp = reinterpret_cast<int *>(xb + n);
+  int *s_ci = s_rp + n + 1;
+  for (int k = threadIdx.x; k < nnz; k += blockDim.x) {
+    s_val[k] = val[k];
+    s_ci[k] = ci[k];
+  }
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) s_rp[i] = rp[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    s_dinv[i] = dinv[i];
+    s_b[i] = b[i];
+    xa[i] = V(0);
+  }
+  __syncthreads();
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      V dot = V(0);
+      for (int k = s_rp[i]; k < s_rp[i + 1]; ++k) dot += s_val[k] * xa[s_ci[k]];
+      xb[i] = xa[i] + s_dinv[i] * (s_b[i] - dot);
+    }
+    __syncthreads();
+    V *t = xa; xa = xb; xb = t;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xa[i];
+}
+
+template <class V>
+static size_t coarse_smem_bytes(int n, long long nnz) {
+  return (size_t)nnz * (sizeof(V) + sizeof(int)) + (size_t)n * 4 * sizeof(V) + ((size_t)n + 1) * sizeof(int);
+}
+constexpr size_t kCoarseSmemMax = 200 * 1024;
+
 template <class V>
 amg_status coarse_solve_block(const CsrView<V> &A, const V *dinv, const V *b, V *x, int sweeps, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
@@ -188,8 +388,90 @@ amg_status coarse_solve_block(const CsrView<V> &A, const V *dinv, const V *b, V 
     return AMG_ERR_UNSUPPORTED;
   }
   CWM_TRACE("coarse", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
-  const size_t sm = 2 * (size_t)A.n * sizeof(V);
-  k_coarse_block<V><<<1, 1024, sm, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, sweeps);
+  const size_t big = coarse_smem_bytes<V>(A.n, A.nnz);
+  if (big <= kCoarseSmemMax) {
+    static bool attr[64] = {false};
+    int dev = 0;
+    CWM_CUDA(cudaGetDevice(&dev));
+    if (!attr[dev & 63]) {
+      CWM_CUDA(cudaFuncSetAttribute(k_coarse_smem<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kCoarseSmemMax));
+      attr[dev & 63] = true;
+    }
+    k_coarse_smem<V><<<1, 1024, big, s>>>(A.n, (int)A.nnz, A.rp, A.ci, A.val, dinv, b, x, sweeps);
+  } else {
+    const size_t sm = 2 * (size_t)A.n * sizeof(V);
+    k_coarse_block<V><<<1, 1024, sm, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, sweeps);
+  }
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ dense coarsest operator ----
+// `sweeps` l1-Jacobi sweeps from zero are the fixed linear map
+//   x = B b,  B = sum_{k < sweeps} (I - D^{-1} A)^k D^{-1},
+// built once at setup by running the sweeps on every unit vector at once (X <- X + D^{-1}(I - A X),
+// X_0 = 0, one thread per entry of the row-major X).  Applying it is then one dense
+// matrix-vector product spread over many SMs, instead of `sweeps` dependent passes inside one
+// block (FP64 throughput per SM is small on GB300).
+__global__ void k_dense_sweep(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const double *__restrict__ val, const double *__restrict__ dinv,
+                              const double *__restrict__ X, double *__restrict__ Y, int first) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = (int)(idx / n), c = (int)(idx % n);
+  const double e = i == c ? 1.0 : 0.0;
+  if (first) {  // X_0 = 0: X_1 = D^{-1}
+    Y[idx] = dinv[i] * e;
+    return;
+  }
+  double s = 0.0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s = fma(val[k], X[(long long)ci[k] * n + c], s);
+  Y[idx] = X[idx] + dinv[i] * (e - s);
+}
+
+amg_status dense_coarse_build(const CsrView<double> &A, const double *dinv, int sweeps, double *X, double *tmp,
+                              cudaStream_t s) {
+  const long long nn = (long long)A.n * A.n;
+  if (nn == 0) return AMG_OK;
+  CWM_TRACE("dense_coarse_build", 8.0 * nn * 2.0 * sweeps, s);
+  if (sweeps <= 0) {
+    CWM_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * nn, s));
+    return AMG_OK;
+  }
+  // ping-pong so that the last sweep lands in X
+  double *bufs[2] = {(sweeps % 2) ? X : tmp, (sweeps % 2) ? tmp : X};
+  const int g = grid_for(nn, kBlock, 1 << 30);
+  for (int k = 0; k < sweeps; ++k) {
+    const double *src = bufs[(k + 1) & 1];
+    double *dst = bufs[k & 1];
+    k_dense_sweep<<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, src, dst, k == 0);
+    CWM_LAUNCH();
+  }
+  return AMG_OK;
+}
+
+// y = X b, one warp per row of X (row-major)
+template <class V>
+__global__ void k_dense_matvec(int n, const V *__restrict__ X, const V *__restrict__ b, V *__restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = warp; i < n; i += nw) {
+    const V *row = X + i * n;
+    V acc = V(0);
+    for (int c = lane; c < n; c += 32) acc = fma(row[c], b[c], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[i] = acc;
+  }
+}
+
+template <class V>
+amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  CWM_TRACE("coarse", (double)sizeof(V) * ((double)n * n + 2.0 * n), s);
+  k_dense_matvec<V><<<grid_for((long long)n * 32, 128, 1 << 30), 128, 0, s>>>(n, X, b, y);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -210,7 +492,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restric
 amg_status residual(const CsrView<double> &A, const double *b, const double *x, double *r, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("residual", 4.0 * (A.n + 1) + 12.0 * A.nnz + 24.0 * A.n, s);
-  CWM_DISPATCH_T(A.tile, (k_residual<kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r)));
+  k_resid_rb<double><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -230,10 +512,20 @@ __global__ void __launch_bounds__(kBlock) k_l1(int n, const int *__restrict__ rp
   }
 }
 
+__global__ void __launch_bounds__(kRB) k_l1_rb(int n, const int *__restrict__ rp, const double *__restrict__ val,
+                                               double *__restrict__ d) {
+  __shared__ RowBlockSmem<double> sm;
+  const int r0 = blockIdx.x * kRB;
+  const int nrows = min(kRB, n - r0);
+  rb_stage_rp(rp, r0, nrows, sm.rp);
+  const double a = rb_row_dot<double, true>(nullptr, val, nullptr, nrows, sm);
+  if (threadIdx.x < nrows) d[r0 + threadIdx.x] = a;
+}
+
 amg_status l1_norms(const CsrView<double> &A, double *d, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("l1_norms", 4.0 * (A.n + 1) + 8.0 * A.nnz + 8.0 * A.n, s);
-  CWM_DISPATCH_T(A.tile, (k_l1<kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.val, d)));
+  k_l1_rb<<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.val, d);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -254,10 +546,9 @@ amg_status reciprocal(int n, const double *x, double *y, float *y32, cudaStream_
 }
 
 // ------------------------------------------------------------ FCG ----
-int fcg_partial_blocks(int n) {
-  (void)n;
-  return num_sms() * 8;
-}
+int fcg_partial_blocks(int n) { return rb_grid(n > 0 ? n : 1); }
+constexpr int kUpdChunk = 8 * kRB;  // entries per fcg_update block
+int fcg_update_blocks(int n) { return (int)(((n > 0 ? n : 1) + kUpdChunk - 1LL) / kUpdChunk); }
 
 // v = A w fused with the three dot products of Algorithm 3 (w is read once per row).
 template <int T>
@@ -288,11 +579,94 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
-amg_status spmv_dots(const CsrView<double> &A, const double *w, const double *r, const double *q, double *v,
-                     double *part, cudaStream_t s) {
-  const int g = fcg_partial_blocks(A.n);
+// The block that finishes last (atomic ticket after a fence) reduces every block's partial
+// sums in block order -- a fixed order, so the result does not depend on scheduling -- and
+// resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned *tick) {
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(tick, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+__device__ __forceinline__ void fcg_scalars_from(int nb, const double *part, double *scal, int first) {
+  double a = 0.0, b = 0.0, g = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a += __ldcg(part + 3 * i);
+    b += __ldcg(part + 3 * i + 1);
+    g += __ldcg(part + 3 * i + 2);
+  }
+  {
+    const double in3[3] = {a, b, g};
+    double o3[3];
+    block_sums<3>(in3, o3);
+    a = o3[0];
+    b = o3[1];
+    g = o3[2];
+  }
+  if (threadIdx.x == 0) {
+    double rho, coef;
+    if (first) {
+      rho = b;
+      coef = 0.0;
+      g = 0.0;
+    } else {
+      const double rp = scal[kRhoPrev];
+      rho = b - g * g / rp;
+      coef = g / rp;
+    }
+    scal[kAlpha] = a;
+    scal[kBeta] = b;
+    scal[kGamma] = g;
+    scal[kRho] = rho;
+    scal[kCoef] = coef;
+    scal[kStep] = a / rho;
+    scal[kRhoPrev] = rho;
+    if (!(rho > 0.0) || !isfinite(rho) || !isfinite(a)) scal[kFlags] = 1.0;
+  }
+}
+
+__global__ void __launch_bounds__(kRB)
+    k_spmv_dots_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ val,
+                   const double *__restrict__ w, const double *__restrict__ r, const double *__restrict__ q,
+                   double *__restrict__ v, double *__restrict__ part, double *scal, unsigned *tick, int first) {
+  __shared__ RowBlockSmem<double> sm;
+  const int r0 = blockIdx.x * kRB;
+  const int nrows = min(kRB, n - r0);
+  rb_stage_rp(rp, r0, nrows, sm.rp);
+  const double dot = rb_row_dot<double, false>(ci, val, w, nrows, sm);
+  double sa = 0.0, sb = 0.0, sg = 0.0;
+  const int i = r0 + threadIdx.x;
+  if (threadIdx.x < nrows) {
+    v[i] = dot;
+    const double wi = w[i];
+    sa = wi * r[i];
+    sb = wi * dot;
+    if (q) sg = wi * q[i];
+  }
+  const double in3[3] = {sa, sb, sg};
+  double t3[3];
+  block_sums<3>(in3, t3);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x + 0] = t3[0];
+    part[3 * blockIdx.x + 1] = t3[1];
+    part[3 * blockIdx.x + 2] = t3[2];
+  }
+  if (last_block(tick)) {
+    fcg_scalars_from(gridDim.x, part, scal, first);
+    if (threadIdx.x == 0) *tick = 0u;
+  }
+}
+
+amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const double *r, const double *q,
+                             double *v, double *part, double *scal, unsigned *tick, int first, cudaStream_t s) {
   CWM_TRACE("spmv_dots", 4.0 * (A.n + 1) + 12.0 * A.nnz + (q ? 32.0 : 24.0) * A.n, s);
-  CWM_DISPATCH_T(A.tile, (k_spmv_dots<kT><<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r, q, v, part)));
+  k_spmv_dots_rb<<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r, q, v, part, scal, tick, first);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -340,28 +714,77 @@ amg_status fcg_scalars(int nb, const double *part, double *scal, int first, cuda
 __global__ void __launch_bounds__(kBlock)
     k_fcg_update(int n, const double *__restrict__ w, const double *__restrict__ v, double *__restrict__ d,
                  double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
-                 const double *__restrict__ scal, double *__restrict__ part, int first) {
-  if (scal[kFlags] != 0.0) return;  // breakdown: leave x, r, d, q as they were
+                 double *__restrict__ scal, double *__restrict__ part, unsigned *tick, int first, int vec) {
+  const bool broken = scal[kFlags] != 0.0;  // breakdown: leave x, r, d, q as they were
   const double coef = scal[kCoef], step = scal[kStep];
   double rr = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double di = first ? w[i] : w[i] - coef * d[i];
-    const double qi = first ? v[i] : v[i] - coef * q[i];
-    d[i] = di;
-    q[i] = qi;
-    x[i] = x[i] + step * di;
-    const double ri = r[i] - step * qi;
-    r[i] = ri;
-    rr += ri * ri;
+  // the block owns kUpdChunk consecutive entries: four coalesced double2 steps per thread
+  const long long base = (long long)blockIdx.x * kUpdChunk;
+  if (!broken) {
+#pragma unroll
+    for (int m = 0; m < kUpdChunk / (2 * kRB); ++m) {
+      const long long i = base + 2 * (threadIdx.x + (long long)m * kRB);
+      if (vec && i + 1 < n) {
+        const double2 w2 = *reinterpret_cast<const double2 *>(w + i);
+        const double2 v2 = *reinterpret_cast<const double2 *>(v + i);
+        const double2 x2 = *reinterpret_cast<const double2 *>(x + i);
+        const double2 r2 = *reinterpret_cast<const double2 *>(r + i);
+        double2 d2, q2;
+        if (first) {
+          d2 = w2;
+          q2 = v2;
+        } else {
+          const double2 dd = *reinterpret_cast<const double2 *>(d + i);
+          const double2 qq = *reinterpret_cast<const double2 *>(q + i);
+          d2 = make_double2(fma(-coef, dd.x, w2.x), fma(-coef, dd.y, w2.y));
+          q2 = make_double2(fma(-coef, qq.x, v2.x), fma(-coef, qq.y, v2.y));
+        }
+        *reinterpret_cast<double2 *>(d + i) = d2;
+        *reinterpret_cast<double2 *>(q + i) = q2;
+        *reinterpret_cast<double2 *>(x + i) = make_double2(fma(step, d2.x, x2.x), fma(step, d2.y, x2.y));
+        const double2 rn = make_double2(fma(-step, q2.x, r2.x), fma(-step, q2.y, r2.y));
+        *reinterpret_cast<double2 *>(r + i) = rn;
+        rr = fma(rn.x, rn.x, rr);
+        rr = fma(rn.y, rn.y, rr);
+      } else {
+        for (long long j = i; j < i + 2 && j < n; ++j) {
+          const double dj = first ? w[j] : fma(-coef, d[j], w[j]);
+          const double qj = first ? v[j] : fma(-coef, q[j], v[j]);
+          d[j] = dj;
+          q[j] = qj;
+          x[j] = fma(step, dj, x[j]);
+          const double rj = fma(-step, qj, r[j]);
+          r[j] = rj;
+          rr = fma(rj, rj, rr);
+        }
+      }
+    }
   }
-  const double t = block_sum(rr);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  {
+    const double in1[1] = {rr};
+    double o1[1];
+    block_sums<1>(in1, o1);
+    if (threadIdx.x == 0) part[blockIdx.x] = o1[0];
+  }
+  if (last_block(tick)) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += __ldcg(part + b);
+    const double in1[1] = {a};
+    double o1[1];
+    block_sums<1>(in1, o1);
+    if (threadIdx.x == 0) {
+      scal[kRR] = o1[0];
+      *tick = 0u;
+    }
+  }
 }
 
 amg_status fcg_update(int n, const double *w, const double *v, double *d, double *q, double *x, double *r,
-                      const double *scal, double *part, int first, cudaStream_t s) {
+                      double *scal, double *part, unsigned *tick, int first, cudaStream_t s) {
   CWM_TRACE("fcg_update", (first ? 64.0 : 80.0) * n, s);
-  k_fcg_update<<<fcg_partial_blocks(n), kBlock, 0, s>>>(n, w, v, d, q, x, r, scal, part, first);
+  auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+  const int vec = al(w) && al(v) && al(d) && al(q) && al(x) && al(r);
+  k_fcg_update<<<fcg_update_blocks(n), kRB, 0, s>>>(n, w, v, d, q, x, r, scal, part, tick, first, vec);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -389,7 +812,7 @@ __global__ void __launch_bounds__(kBlock) k_sqnorm(int n, const double *__restri
 
 amg_status sqnorm_partials(int n, const double *a, double *part, cudaStream_t s) {
   CWM_TRACE("sqnorm", 8.0 * n, s);
-  k_sqnorm<<<fcg_partial_blocks(n), kBlock, 0, s>>>(n, a, part);
+  k_sqnorm<<<fcg_partial_blocks(n), kRB, 0, s>>>(n, a, part);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -422,7 +845,10 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
   template amg_status resid_restrict<V>(const CsrView<V> &, int, const int *, const int *, const V *,        \
                                         const V *, const V *, V *, cudaStream_t);                            \
   template amg_status prolong<V>(int, const int *, const V *, const V *, const V *, V *, cudaStream_t);      \
-  template amg_status coarse_solve_block<V>(const CsrView<V> &, const V *, const V *, V *, int, cudaStream_t);
+  template amg_status resid_restrict_rb<V>(const CsrView<V> &, int, const int *, const int *, const V *,     \
+                                           const V *, const V *, V *, V *, cudaStream_t);                    \
+  template amg_status coarse_solve_block<V>(const CsrView<V> &, const V *, const V *, V *, int, cudaStream_t); \
+  template amg_status dense_coarse_apply<V>(int, const V *, const V *, V *, cudaStream_t);
 CWM_INST(double)
 CWM_INST(float)
 

@@ -30,6 +30,18 @@ amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V 
 template <class V>
 amg_status resid_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                           const V *b, const V *x, V *bc, cudaStream_t s);
+// Largest coarsest level whose sweeps are turned into a dense operator at setup.
+constexpr int kDenseCoarseMax = 2048;
+// X (n*n, row-major) = the linear map of `sweeps` l1-Jacobi sweeps from zero; tmp: n*n
+amg_status dense_coarse_build(const CsrView<double> &A, const double *dinv, int sweeps, double *X, double *tmp,
+                              cudaStream_t s);
+// y = X b
+template <class V>
+amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t s);
+// r = b - A x into r_scratch (row blocks), then bc[I] = sum_{m in I} p_m r_m
+template <class V>
+amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
+                             const V *b, const V *x, V *r_scratch, V *bc, cudaStream_t s);
 // y = x + p .* xc[agg]; x may be NULL (0)
 template <class V>
 amg_status prolong(int n, const int *agg, const V *p, const V *xc, const V *x, V *y, cudaStream_t s);
@@ -42,15 +54,18 @@ amg_status residual(const CsrView<double> &A, const double *b, const double *x, 
 
 // FCG device scalars (one array of doubles on the device).
 enum FcgSlot { kAlpha = 0, kBeta, kGamma, kRho, kRhoPrev, kCoef, kStep, kRR, kBB, kFlags, kFcgSlots };
-int fcg_partial_blocks(int n);
-// v = A w and per-block partial sums of w.r, w.v, w.q (q may be NULL) into part[3 * nb]
-amg_status spmv_dots(const CsrView<double> &A, const double *w, const double *r, const double *q, double *v,
-                     double *part, cudaStream_t s);
+int fcg_partial_blocks(int n);   // partial sums written by spmv_dots and sqnorm_partials
+int fcg_update_blocks(int n);    // partial sums written by fcg_update
+// v = A w with per-block partial sums of w.r, w.v, w.q (q may be NULL) into part[3 * nb];
+// the last block to finish turns them into alpha, beta, gamma, rho, coef = gamma/rho_prev
+// and step = alpha/rho in scal (tick: a zeroed counter, left zeroed)
+amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const double *r, const double *q,
+                             double *v, double *part, double *scal, unsigned *tick, int first, cudaStream_t s);
 // scalars from the partials: alpha, beta, gamma, rho, coef = gamma/rho_prev, step = alpha/rho
 amg_status fcg_scalars(int nb, const double *part, double *scal, int first, cudaStream_t s);
-// d = w - coef d; q = v - coef q; x += step d; r -= step q; partial sums of r.r into part[nb]
+// d = w - coef d; q = v - coef q; x += step d; r -= step q; r.r into scal[kRR] (last block)
 amg_status fcg_update(int n, const double *w, const double *v, double *d, double *q, double *x, double *r,
-                      const double *scal, double *part, int first, cudaStream_t s);
+                      double *scal, double *part, unsigned *tick, int first, cudaStream_t s);
 // scal[slot] = sum of part[0..nb)
 amg_status reduce_into(int nb, const double *part, double *scal, int slot, cudaStream_t s);
 // partial sums of a.a into part[nb]
