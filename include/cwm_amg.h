@@ -54,12 +54,17 @@ typedef struct {
   int check_input;      /* 1: amg_setup verifies CSR structure and bit symmetry of A on
                            the device before coarsening (default 1) */
   int keep_sweeps;      /* 1: keep every sweep's matching for amg_sweep_mate (default 0) */
-  int64_t loop_cap;     /* cap on iterations of any one device retry loop; 0 = derived
-                           from the matrix size (never reached by valid input) */
+  int64_t loop_cap;     /* cap on iterations of any one device retry loop or wait (Suitor
+                           proposal chains, grid-barrier polls in the V-cycle); 0 = derived
+                           from the sizes (never reached by valid input) */
   int trace;            /* 1: time kernel classes from the start of amg_setup (see
                            amg_trace_*); 0: no tracing (default 0) */
   char trace_filter[32];/* with trace = 1: only classes whose name starts with this
                            NUL-terminated prefix ("" = every class) */
+  int tail_rows;        /* levels with at most this many rows (down to the coarsest) run
+                           as one cooperative launch per V-cycle; 0 = 65536, -1 = never
+                           (default -1: on GB300 the grid barriers cost more than the
+                           small launches they replace) */
 } amg_params;
 
 /* Statistics filled by amg_pcg_solve and amg_stats. */

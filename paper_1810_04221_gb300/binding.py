@@ -43,6 +43,7 @@ class AmgParams(C.Structure):
         ("loop_cap", C.c_int64),
         ("trace", C.c_int),
         ("trace_filter", C.c_char * 32),
+        ("tail_rows", C.c_int),
     ]
 
 

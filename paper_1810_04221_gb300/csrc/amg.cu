@@ -93,6 +93,33 @@ struct amg_hierarchy {
   DBuf<unsigned> tick;  // last-block tickets of the fused reductions (kept at zero between launches)
   double t_setup_ms = 0.0, t_solve_ms = 0.0;
   Tracer trace;
+  // the FCG iteration replayed as CUDA graphs on a library-owned stream
+  cudaStream_t solve_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [0]: iterations >= 1, [1]: the first
+  std::vector<Tracer::Pending> gscopes[2];        // tracer scopes recorded inside each graph
+  double *graph_x = nullptr;                      // the solution pointer the graphs use
+  bool graphs_failed = false;
+  // the fused coarse end of the V-cycle
+  int tail_start = -1;  // first level run by vcycle_tail, -1: none
+  TailArgs<double> tail64{};
+  TailArgs<float> tail32{};
+  DBuf<unsigned> bar;   // grid-barrier state (count, generation)
+  DBuf<unsigned char> tail_dev;  // device copies of tail64 and tail32
+  void drop_graphs() {
+    for (int g = 0; g < 2; ++g) {
+      if (gexec[g]) cudaGraphExecDestroy(gexec[g]);
+      gexec[g] = nullptr;
+      trace.release(gscopes[g]);
+    }
+    graph_x = nullptr;
+  }
+  ~amg_hierarchy() {
+    drop_graphs();
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (solve_stream) cudaStreamDestroy(solve_stream);
+  }
 };
 
 namespace {
@@ -126,6 +153,18 @@ amg_status read_err(amg_hierarchy *h, const char *where) {
     return status_from_device_bits(bits, where);
   }
   return AMG_OK;
+}
+
+// A device error raised inside the solve (a bounded wait that gave up): report it and reset
+// the error word and the grid-barrier state for later calls.
+amg_status solve_device_error(amg_hierarchy *h, const char *where) {
+  const int bits = h->box.ints[8];
+  if (!bits) return AMG_OK;
+  cudaMemsetAsync(h->err.get(), 0, sizeof(int), h->stream);
+  if (h->bar.get()) cudaMemsetAsync(h->bar.get(), 0, 2 * sizeof(unsigned), h->stream);
+  cudaStreamSynchronize(h->stream);
+  h->box.ints[8] = 0;
+  return status_from_device_bits(bits, where);
 }
 
 long long default_cap(const amg_params &prm, long long n, long long nnz) {
@@ -283,6 +322,8 @@ amg_status finish_level(amg_hierarchy *h, Level &L) {
 // ------------------------------------------------------------ V-cycle ----
 template <class V>
 struct LevelVec;
+template <class V>
+TailArgs<V> &tail_args(amg_hierarchy *h);
 template <>
 struct LevelVec<double> {
   static CsrView<double> A(const Level &L) { return L.view64(); }
@@ -306,6 +347,52 @@ struct LevelVec<float> {
   static const float *dense(const Level &L) { return L.xdense32.get(); }
 };
 
+template <>
+TailArgs<double> &tail_args<double>(amg_hierarchy *h) { return h->tail64; }
+template <>
+TailArgs<float> &tail_args<float>(amg_hierarchy *h) { return h->tail32; }
+template <class V>
+const TailArgs<V> *tail_dev_args(amg_hierarchy *h);
+template <>
+const TailArgs<double> *tail_dev_args<double>(amg_hierarchy *h) {
+  return reinterpret_cast<const TailArgs<double> *>(h->tail_dev.get());
+}
+template <>
+const TailArgs<float> *tail_dev_args<float>(amg_hierarchy *h) {
+  return reinterpret_cast<const TailArgs<float> *>(h->tail_dev.get() + sizeof(TailArgs<double>));
+}
+
+template <class V>
+void fill_tail(amg_hierarchy *h, int k0, TailArgs<V> &a) {
+  using LV = LevelVec<V>;
+  a.nlev = (int)h->lev.size() - k0;
+  a.pre = h->prm.pre_sweeps;
+  a.post = h->prm.post_sweeps;
+  a.coarse_sweeps = h->prm.coarse_sweeps;
+  a.spin_cap = h->prm.loop_cap > 0 ? (unsigned)(h->prm.loop_cap < (1ll << 31) ? h->prm.loop_cap : (1ll << 31))
+                                   : (1u << 24);
+  for (int l = 0; l < a.nlev; ++l) {
+    Level &L = h->lev[k0 + l];
+    TailLevel<V> &t = a.lev[l];
+    const CsrView<V> A = LV::A(L);
+    t.n = L.n;
+    t.rp_host_nnz = L.nnz;
+    t.rp = A.rp;
+    t.ci = A.ci;
+    t.val = A.val;
+    t.dinv = LV::dinv(L);
+    t.agg = L.agg.get();
+    t.mptr = L.mptr.get();
+    t.mlist = L.mlist.get();
+    t.p = LV::p(L);
+    t.b = LV::b(L);
+    t.x = LV::x(L);
+    t.t1 = LV::t1(L);
+    t.t2 = LV::t2(L);
+    t.dense = LV::dense(L);
+  }
+}
+
 // x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
 template <class V>
 amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
@@ -313,6 +400,8 @@ amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
   cudaStream_t s = h->stream;
   Level &L = h->lev[k];
   LevelTag tag(k);
+  if (k == h->tail_start)
+    return vcycle_tail<V>(tail_args<V>(h), tail_dev_args<V>(h), b, x, h->bar.get(), h->err.get(), s);
   const CsrView<V> A = LV::A(L);
   const V *dinv = LV::dinv(L);
   V *t1 = LV::t1(L), *t2 = LV::t2(L);
@@ -394,6 +483,7 @@ void amg_default_params(amg_params *p) {
   p->keep_sweeps = 0;
   p->loop_cap = 0;
   p->trace = 0;
+  p->tail_rows = -1;
 }
 
 const char *amg_status_string(amg_status s) {
@@ -485,6 +575,26 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
     }
   }
 
+  // the fused coarse end of the V-cycle
+  {
+    const int nl = (int)h->lev.size();
+    const int limit = P.tail_rows > 0 ? P.tail_rows : (P.tail_rows == 0 ? kTailMaxRows : -1);
+    // measured on GB300 with the default cycle, the cooperative launch and its grid barriers
+    // cost more than the small kernels they replace, so the tail is opt-in (tail_rows > 0)
+    int k0 = nl;
+    while (limit > 0 && k0 > 0 && h->lev[k0 - 1].n <= limit) --k0;
+    if (k0 < nl && nl - k0 <= kTailMaxLevels) {
+      h->tail_start = k0;
+      CWM_TRY(h->bar.alloc(2, s));
+      CWM_CUDA(cudaMemsetAsync(h->bar.get(), 0, 2 * sizeof(unsigned), s));
+      fill_tail<double>(h, k0, h->tail64);
+      if (P.vcycle_fp32) fill_tail<float>(h, k0, h->tail32);
+      CWM_TRY(h->tail_dev.alloc(sizeof(TailArgs<double>) + sizeof(TailArgs<float>), s));
+      CWM_CUDA(cudaMemcpyAsync(h->tail_dev.get(), &h->tail64, sizeof(TailArgs<double>), cudaMemcpyHostToDevice, s));
+      CWM_CUDA(cudaMemcpyAsync(h->tail_dev.get() + sizeof(TailArgs<double>), &h->tail32, sizeof(TailArgs<float>),
+                               cudaMemcpyHostToDevice, s));
+    }
+  }
   // FCG work vectors
   CWM_TRY(h->r.alloc(n, s));
   CWM_TRY(h->w.alloc(n, s));
@@ -497,6 +607,9 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   CWM_TRY(h->scal.alloc(kFcgSlots, s));
   CWM_TRY(h->tick.alloc(4, s));
   CWM_CUDA(cudaMemsetAsync(h->tick.get(), 0, 4 * sizeof(unsigned), s));
+  CWM_CUDA(cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking));
+  CWM_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CWM_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
   CWM_CUDA(cudaStreamSynchronize(s));
   return AMG_OK;
 }
@@ -625,12 +738,71 @@ amg_status amg_vcycle(amg_handle h, const double *d_r, double *d_w, void *stream
   h->stream = (cudaStream_t)stream;
   TraceGuard tg(h);
   amg_status st = apply_vcycle(h, d_r, d_w);
+  if (st == AMG_OK && h->tail_start >= 0) {  // the fused tail has a bounded wait: check it
+    cudaError_t e = cudaMemcpyAsync(h->box.ints + 8, h->err.get(), sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    st = e == cudaSuccess ? solve_device_error(h, "amg_vcycle") : cuda_fail(e, "amg_vcycle", __FILE__, __LINE__);
+  }
   h->stream = prev;
   return st;
 }
 
-amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rtol, int itmax, void *stream,
-                         amg_info *info) {
+}  // extern "C"
+
+namespace {
+
+// One FCG iteration (Algorithm 3): w = B(r), v = A w with the three dot products and the
+// scalars, the paired updates with ||r||^2, and the copy of the scalars to the host.
+amg_status fcg_iteration(amg_hierarchy *h, double *d_x, int first) {
+  cudaStream_t s = h->stream;
+  const Level &L0 = h->lev[0];
+  const CsrView<double> A = L0.view64();
+  double *scal = h->scal.get();
+  CWM_TRY(apply_vcycle(h, h->r.get(), h->w.get()));
+  CWM_TRY(spmv_dots_scalars(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
+                            scal, h->tick.get(), first, s));
+  CWM_TRY(fcg_update(L0.n, h->w.get(), h->vv.get(), h->d.get(), h->q.get(), d_x, h->r.get(), scal, h->part2.get(),
+                     h->tick.get() + 1, first, s));
+  CWM_CUDA(cudaMemcpyAsync(h->box.dbls, scal, sizeof(double) * kFcgSlots, cudaMemcpyDeviceToHost, s));
+  CWM_CUDA(cudaMemcpyAsync(h->box.ints + 8, h->err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  return AMG_OK;
+}
+
+// Captures the two iteration graphs (first / later iterations) for solution pointer d_x.
+// On any capture failure the solver falls back to plain launches for this handle.
+void capture_graphs(amg_hierarchy *h, double *d_x) {
+  h->drop_graphs();
+  if (h->graphs_failed) return;
+  for (int g = 0; g < 2; ++g) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      h->graphs_failed = true;
+      break;
+    }
+    h->trace.capturing = true;
+    amg_status st = fcg_iteration(h, d_x, g);
+    h->trace.capturing = false;
+    h->gscopes[g].swap(h->trace.graph_pending);
+    h->trace.graph_pending.clear();
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (st != AMG_OK || e != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&h->gexec[g], graph, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      h->graphs_failed = true;
+      break;
+    }
+    cudaGraphDestroy(graph);
+  }
+  if (h->graphs_failed) h->drop_graphs();
+  else h->graph_x = d_x;
+}
+
+}  // namespace
+
+extern "C" amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rtol, int itmax,
+                                    void *stream, amg_info *info) {
   CWM_TRY(validate_handle(h));
   if (!d_b || !d_x || itmax < 0 || !(rtol >= 0.0)) {
     set_error("amg_pcg_solve: invalid argument");
@@ -638,14 +810,18 @@ amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rt
   }
   const double t0 = now_ms();
   cudaStream_t prev = h->stream;
-  cudaStream_t s = (cudaStream_t)stream;
-  h->stream = s;
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t s = h->solve_stream;
   struct Restore {
     amg_hierarchy *h;
     cudaStream_t s;
     ~Restore() { h->stream = s; }
   } restore{h, prev};
+  h->stream = s;
   TraceGuard tg(h);
+  // order after the caller's stream, run on the library's stream
+  CWM_CUDA(cudaEventRecord(h->ev_in, user));
+  CWM_CUDA(cudaStreamWaitEvent(s, h->ev_in, 0));
 
   const Level &L0 = h->lev[0];
   const CsrView<double> A = L0.view64();
@@ -663,16 +839,22 @@ amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rt
   const double nb2 = std::sqrt(h->box.dbls[kBB]);
   double nr = std::sqrt(h->box.dbls[kRR]);
   amg_status status = (nb2 == 0.0 || nr <= rtol * nb2) ? AMG_OK : AMG_ERR_NOT_CONVERGED;
+  if (status != AMG_OK && itmax > 0 && h->graph_x != d_x) capture_graphs(h, d_x);
   int it = 0;
   while (status != AMG_OK && it < itmax) {
     const int first = it == 0;
-    CWM_TRY(apply_vcycle(h, h->r.get(), h->w.get()));
-    CWM_TRY(spmv_dots_scalars(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
-                              scal, h->tick.get(), first, s));
-    CWM_TRY(fcg_update(n, h->w.get(), h->vv.get(), h->d.get(), h->q.get(), d_x, h->r.get(), scal, h->part2.get(),
-                       h->tick.get() + 1, first, s));
-    CWM_CUDA(cudaMemcpyAsync(h->box.dbls, scal, sizeof(double) * kFcgSlots, cudaMemcpyDeviceToHost, s));
-    CWM_CUDA(cudaStreamSynchronize(s));
+    if (h->gexec[first] && h->graph_x == d_x) {
+      CWM_CUDA(cudaGraphLaunch(h->gexec[first], s));
+      CWM_CUDA(cudaStreamSynchronize(s));
+      if (h->trace.on) h->trace.collect(h->gscopes[first]);
+    } else {
+      CWM_TRY(fcg_iteration(h, d_x, first));
+      CWM_CUDA(cudaStreamSynchronize(s));
+    }
+    {
+      const amg_status dst = solve_device_error(h, "amg_pcg_solve");
+      if (dst != AMG_OK) return dst;
+    }
     if (h->box.dbls[kFlags] != 0.0) {
       status = AMG_ERR_BREAKDOWN;
       set_error("amg_pcg_solve: breakdown at iteration %d (rho = %g)", it, h->box.dbls[kRho]);
@@ -686,9 +868,11 @@ amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rt
   // true residual
   CWM_TRY(residual(A, d_b, d_x, h->vv.get(), s));
   CWM_TRY(sqnorm_partials(n, h->vv.get(), h->part2.get(), s));
-  CWM_TRY(reduce_into(nb, h->part2.get(), scal, kBB + 0, s));  // reuse slot: true ||r||^2
+  CWM_TRY(reduce_into(nb, h->part2.get(), scal, kBB, s));  // slot reused: true ||r||^2
   CWM_CUDA(cudaMemcpyAsync(h->box.dbls + 12, scal + kBB, sizeof(double), cudaMemcpyDeviceToHost, s));
   CWM_CUDA(cudaStreamSynchronize(s));
+  CWM_CUDA(cudaEventRecord(h->ev_out, s));
+  CWM_CUDA(cudaStreamWaitEvent(user, h->ev_out, 0));
   const double nr_true = std::sqrt(h->box.dbls[12]);
   h->t_solve_ms = now_ms() - t0;
   if (info) {
@@ -700,6 +884,8 @@ amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x, double rt
   }
   return status;
 }
+
+extern "C" {
 
 // ------------------------------------------------------------ tracing ----
 amg_status amg_trace_enable(amg_handle h, int on, const char *filter) {

@@ -116,12 +116,116 @@ __global__ void __launch_bounds__(256) k_edge_weights(int n, const int *__restri
   }
 }
 
-// Row-block form of the same computation: a block of kWB threads owns kWB consecutive
-// rows and streams their slots in chunks of kWB * kWE with coalesced loads; each slot's
-// row comes from a shared-memory row-id map filled by the row's thread.
+// Row-block form of the same computation, evaluating each edge once.  A block of kWB
+// threads owns kWB consecutive rows.  Each row's thread finds where its upper part
+// (columns > i) starts, writes 0 into its diagonal slot, and the block packs the upper
+// slots of all its rows into one dense list (an exclusive scan of the per-row counts);
+// threads then take that list in chunks of kWC, so the FP64 work -- a pipe that retires
+// whole-warp instructions at a low rate on GB300 -- runs on full warps.  The thread that
+// evaluates slot (i, j) also stores the weight into the mirror slot (j, i), found by a
+// binary search in row j.
 constexpr int kWB = 256;
 constexpr int kWE = 8;
 constexpr int kWC = kWB * kWE;
+
+__global__ void __launch_bounds__(kWB) k_edge_weights_rb(int n, const int *__restrict__ rp,
+                                                         const int *__restrict__ ci,
+                                                         const double *__restrict__ val,
+                                                         const double *__restrict__ dv,
+                                                         const double *__restrict__ v,
+                                                         double *__restrict__ w) {
+  __shared__ double s_v[kWB], s_d[kWB];
+  __shared__ int s_ustart[kWB], s_uoff[kWB + 1];
+  __shared__ int s_slot[kWC];
+  __shared__ unsigned char s_row[kWC];
+  __shared__ int s_wsum[kWB / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int r0 = blockIdx.x * kWB;
+  const int nrows = min(kWB, n - r0);
+  int ucnt = 0, ustart = 0;
+  if (t < nrows) {
+    const int i = r0 + t;
+    const int s = rp[i], e = rp[i + 1];
+    s_v[t] = v[i];
+    s_d[t] = dv[i];
+    int lo = s, hi = e;  // first slot with column >= i
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ci[mid] < i) lo = mid + 1;
+      else hi = mid;
+    }
+    int k = lo;
+    if (k < e && ci[k] == i) {
+      w[k] = 0.0;  // the diagonal carries no edge
+      ++k;
+    }
+    ustart = k;
+    ucnt = e - k;
+  }
+  // block exclusive scan of the upper counts
+  int incl = ucnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  int wbase = 0;
+  for (int q = 0; q < warp; ++q) wbase += s_wsum[q];
+  s_ustart[t] = ustart;
+  s_uoff[t] = wbase + incl - ucnt;
+  if (t == kWB - 1) s_uoff[kWB] = wbase + incl;
+  __syncthreads();
+  const int U = s_uoff[kWB];
+  const int my_s = s_uoff[t], my_e = my_s + ucnt;
+  for (int c0 = 0; c0 < U; c0 += kWC) {
+    const int cend = min(c0 + kWC, U);
+    for (int q = max(my_s, c0); q < min(my_e, cend); ++q) {
+      s_slot[q - c0] = ustart + (q - my_s);
+      s_row[q - c0] = (unsigned char)t;
+    }
+    __syncthreads();
+    int slot[kWE], col[kWE];
+    double a[kWE];
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      const int q = c0 + e * kWB + t;
+      slot[e] = q < cend ? s_slot[q - c0] : -1;
+      col[e] = slot[e] >= 0 ? __ldg(ci + slot[e]) : 0;
+      a[e] = slot[e] >= 0 ? __ldg(val + slot[e]) : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      if (slot[e] < 0) continue;
+      const int il = s_row[c0 + e * kWB + t - c0];
+      const int i = r0 + il, j = col[e];  // i < j: row i is the smaller index
+      double c = 0.0;
+      if (a[e] != 0.0) {
+        const double va = s_v[il], vb = __ldg(v + j);
+        const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a[e]), va), vb);
+        const double den = __dadd_rn(s_d[il], __ldg(dv + j));
+        if (den != 0.0) {
+          const double cc = __dsub_rn(1.0, __ddiv_rn(num, den));
+          if (cc > 0.0) c = cc;
+        }
+      }
+      __stcs(w + slot[e], c);
+      int lo = __ldg(rp + j), hi = __ldg(rp + j + 1) - 1;  // mirror slot (j, i)
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int cm = __ldg(ci + mid);
+        if (cm == i) {
+          __stcs(w + mid, c);
+          break;
+        }
+        if (cm < i) lo = mid + 1;
+        else hi = mid - 1;
+      }
+    }
+    __syncthreads();
+  }
+}
 
 // dv[i] = (a_ii v_i) v_i: the per-vertex half of the denominator, rounded exactly as in
 // the per-slot expression, so that den = dv[a] + dv[b] is bit-identical.
@@ -131,66 +235,6 @@ __global__ void k_vertex_dv(int n, const double *__restrict__ diag, const double
     dv[i] = __dmul_rn(__dmul_rn(diag[i], v[i]), v[i]);
 }
 
-__global__ void __launch_bounds__(kWB) k_edge_weights_rb(int n, const int *__restrict__ rp,
-                                                         const int *__restrict__ ci,
-                                                         const double *__restrict__ val,
-                                                         const double *__restrict__ diag,
-                                                         const double *__restrict__ v,
-                                                         double *__restrict__ w) {
-  // `diag` holds dv = (a_ii v_i) v_i here (see k_vertex_dv)
-  __shared__ int s_rp[kWB + 1];
-  __shared__ double s_v[kWB], s_d[kWB];
-  __shared__ unsigned char s_row[kWC];
-  const int t = threadIdx.x;
-  const int r0 = blockIdx.x * kWB;
-  const int nrows = min(kWB, n - r0);
-  for (int i = t; i <= nrows; i += kWB) s_rp[i] = rp[r0 + i];
-  if (t < nrows) {
-    s_v[t] = v[r0 + t];
-    s_d[t] = diag[r0 + t];
-  }
-  __syncthreads();
-  const int rs = s_rp[0], re = s_rp[nrows];
-  const int my_s = t < nrows ? s_rp[t] : 0, my_e = t < nrows ? s_rp[t + 1] : 0;
-  for (int c0 = rs; c0 < re; c0 += kWC) {
-    const int cend = min(c0 + kWC, re);
-    for (int k = max(my_s, c0); k < min(my_e, cend); ++k) s_row[k - c0] = (unsigned char)t;
-    __syncthreads();
-    int col[kWE];
-    double a[kWE];
-#pragma unroll
-    for (int e = 0; e < kWE; ++e) {
-      const int k = c0 + e * kWB + t;
-      const bool in = k < cend;
-      col[e] = in ? __ldcs(ci + k) : -1;
-      a[e] = in ? __ldcs(val + k) : 0.0;
-    }
-#pragma unroll
-    for (int e = 0; e < kWE; ++e) {
-      if (col[e] < 0) continue;
-      const int k = c0 + e * kWB + t;
-      const int il = s_row[k - c0];
-      const int i = r0 + il, j = col[e];
-      double c = 0.0;
-      if (j != i && a[e] != 0.0) {
-        const double vi = s_v[il], di = s_d[il];
-        const double vj = __ldg(v + j), dj = __ldg(diag + j);
-        const bool lo_i = i < j;
-        const double va = lo_i ? vi : vj, vb = lo_i ? vj : vi;
-        const double da = lo_i ? di : dj, db = lo_i ? dj : di;
-        const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a[e]), va), vb);
-        const double den = __dadd_rn(da, db);
-        if (den != 0.0) {
-          const double cc = __dsub_rn(1.0, __ddiv_rn(num, den));
-          if (cc > 0.0) c = cc;
-        }
-      }
-      __stcs(w + k, c);
-    }
-    __syncthreads();
-  }
-}
-
 amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
                         const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s) {
   if (n == 0) return AMG_OK;
@@ -198,6 +242,8 @@ amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, cons
   CWM_TRACE("weights", 4.0 * (n + 1) + 20.0 * nnz + 32.0 * n, s);
   k_vertex_dv<<<grid_for(n, 256, num_sms() * 8), 256, 0, s>>>(n, diag, v, dv_scratch);
   CWM_LAUNCH();
+  // lower slots without an upper partner (a pattern that is not symmetric) stay 0
+  CWM_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)nnz, s));
   k_edge_weights_rb<<<(n + kWB - 1) / kWB, kWB, 0, s>>>(n, rp, ci, val, dv_scratch, v, w);
   CWM_LAUNCH();
   return AMG_OK;

@@ -56,20 +56,51 @@ TraceScope::TraceScope(const char *cat, double b, cudaStream_t st) : s(st), byte
   t = g_tracer;
   idx = t->entry(name);
   a = t->event();
-  if (a) cudaEventRecord(a, s);
+  // inside a stream capture an external record node is needed for replays to re-record it
+  if (a) {
+    if (t->capturing) cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+    else cudaEventRecord(a, s);
+  }
 }
 
 TraceScope::~TraceScope() {
   if (!t || !a) return;
   cudaEvent_t b = t->event();
   if (!b) return;
-  cudaEventRecord(b, s);
+  if (t->capturing) cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+  else cudaEventRecord(b, s);
+  if (t->capturing) {
+    t->graph_pending.push_back({idx, a, b, bytes});
+    return;
+  }
   t->pending.push_back({idx, a, b, bytes});
   if (t->pending.size() > 4096) t->flush();
 }
 
+void Tracer::collect(const std::vector<Pending> &scopes) {
+  for (const Pending &p : scopes) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      TraceEntry &e = entries[p.idx];
+      e.launches += 1;
+      e.ms += ms;
+      e.bytes += p.bytes;
+    }
+    (void)cudaGetLastError();
+  }
+}
+
+void Tracer::release(std::vector<Pending> &scopes) {
+  for (const Pending &p : scopes) {
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  scopes.clear();
+}
+
 Tracer::~Tracer() {
   flush();
+  release(graph_pending);
   for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 

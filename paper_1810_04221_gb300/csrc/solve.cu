@@ -81,6 +81,7 @@ struct RowBlockSmem {
 
 // Stages the row pointers of rows [r0, r0 + nrows] (all threads call it).
 __device__ __forceinline__ void rb_stage_rp(const int *__restrict__ rp, int r0, int nrows, int *s_rp) {
+  __syncthreads();  // earlier readers of s_rp are done
   for (int i = threadIdx.x; i <= nrows; i += kRB) s_rp[i] = rp[r0 + i];
   __syncthreads();
 }
@@ -546,7 +547,12 @@ amg_status reciprocal(int n, const double *x, double *y, float *y32, cudaStream_
 }
 
 // ------------------------------------------------------------ FCG ----
-int fcg_partial_blocks(int n) { return rb_grid(n > 0 ? n : 1); }
+// blocks of the grid-stride FCG reductions: at most 8 resident blocks per SM
+int fcg_partial_blocks(int n) {
+  const int rb = rb_grid(n > 0 ? n : 1);
+  const int cap = num_sms() * 8;
+  return rb < cap ? rb : cap;
+}
 constexpr int kUpdChunk = 8 * kRB;  // entries per fcg_update block
 int fcg_update_blocks(int n) { return (int)(((n > 0 ? n : 1) + kUpdChunk - 1LL) / kUpdChunk); }
 
@@ -636,18 +642,21 @@ __global__ void __launch_bounds__(kRB)
                    const double *__restrict__ w, const double *__restrict__ r, const double *__restrict__ q,
                    double *__restrict__ v, double *__restrict__ part, double *scal, unsigned *tick, int first) {
   __shared__ RowBlockSmem<double> sm;
-  const int r0 = blockIdx.x * kRB;
-  const int nrows = min(kRB, n - r0);
-  rb_stage_rp(rp, r0, nrows, sm.rp);
-  const double dot = rb_row_dot<double, false>(ci, val, w, nrows, sm);
   double sa = 0.0, sb = 0.0, sg = 0.0;
-  const int i = r0 + threadIdx.x;
-  if (threadIdx.x < nrows) {
-    v[i] = dot;
-    const double wi = w[i];
-    sa = wi * r[i];
-    sb = wi * dot;
-    if (q) sg = wi * q[i];
+  // grid-stride over row blocks: each thread accumulates its rows' contributions, so the
+  // block-wide FP64 reduction is paid once per block, not once per 256 rows
+  for (int r0 = blockIdx.x * kRB; r0 < n; r0 += gridDim.x * kRB) {
+    const int nrows = min(kRB, n - r0);
+    rb_stage_rp(rp, r0, nrows, sm.rp);
+    const double dot = rb_row_dot<double, false>(ci, val, w, nrows, sm);
+    const int i = r0 + threadIdx.x;
+    if (threadIdx.x < nrows) {
+      v[i] = dot;
+      const double wi = w[i];
+      sa = fma(wi, r[i], sa);
+      sb = fma(wi, dot, sb);
+      if (q) sg = fma(wi, q[i], sg);
+    }
   }
   const double in3[3] = {sa, sb, sg};
   double t3[3];
@@ -666,7 +675,7 @@ __global__ void __launch_bounds__(kRB)
 amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const double *r, const double *q,
                              double *v, double *part, double *scal, unsigned *tick, int first, cudaStream_t s) {
   CWM_TRACE("spmv_dots", 4.0 * (A.n + 1) + 12.0 * A.nnz + (q ? 32.0 : 24.0) * A.n, s);
-  k_spmv_dots_rb<<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r, q, v, part, scal, tick, first);
+  k_spmv_dots_rb<<<fcg_partial_blocks(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r, q, v, part, scal, tick, first);
   CWM_LAUNCH();
   return AMG_OK;
 }

@@ -49,6 +49,35 @@ amg_status prolong(int n, const int *agg, const V *p, const V *xc, const V *x, V
 template <class V>
 amg_status coarse_solve_block(const CsrView<V> &A, const V *dinv, const V *b, V *x, int sweeps,
                               cudaStream_t s);
+// The coarse end of the V-cycle in one cooperative launch (tail.cu): every level from
+// the first with at most kTailMaxRows rows down to the coarsest.
+constexpr int kTailMaxRows = 65536;  // default of amg_params.tail_rows
+constexpr int kTailMaxLevels = 12;
+template <class V>
+struct TailLevel {
+  int n;
+  long long rp_host_nnz;  // nnz, for the tracer's byte count
+  const int *rp, *ci;
+  const V *val, *dinv;
+  const int *agg, *mptr, *mlist;  // transfer to the next level (unused on the coarsest)
+  const V *p;
+  V *b, *x, *t1, *t2;
+  const V *dense;  // coarsest only: the dense operator of the coarse sweeps, or NULL
+};
+template <class V>
+struct TailArgs {
+  int nlev;
+  int pre, post, coarse_sweeps;
+  unsigned spin_cap;  // bound on each grid-barrier wait (polls)
+  int grid;           // blocks of the cooperative launch (0: one per SM)
+  TailLevel<V> lev[kTailMaxLevels];
+};
+// x0 = V-cycle of the tail's first level applied to b0; bar: two zeroed unsigned ints (grid
+// barrier), err: the device error word
+// (a: the host copy, d_a: the same table in device memory)
+template <class V>
+amg_status vcycle_tail(const TailArgs<V> &a, const TailArgs<V> *d_a, const V *b0, V *x0, unsigned *bar, int *err,
+                       cudaStream_t s);
 // r = b - A x
 amg_status residual(const CsrView<double> &A, const double *b, const double *x, double *r, cudaStream_t s);
 

@@ -27,7 +27,15 @@ struct Tracer {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
+  // while a stream capture is recorded, scopes land here: their events are re-recorded by
+  // every replay of the graph and read back by collect_graph() after each replay
+  bool capturing = false;
+  std::vector<Pending> graph_pending;
   ~Tracer();
+  // after a replay of a graph has completed: fold that graph's scopes in
+  void collect(const std::vector<Pending> &scopes);
+  // the graph is destroyed: recycle its events
+  void release(std::vector<Pending> &scopes);
   bool wants(const char *cat) const;
   int entry(const char *cat);
   cudaEvent_t event();

@@ -1,0 +1,100 @@
+"""GPU: V-cycle variants against the oracle -- the fused coarse tail on and off, other
+pre/post sweep counts, and the float32 V-cycle inside the float64 FCG.
+
+Tolerances: float64 V-cycle 1e-12 relative (summation order differs from the oracle's);
+float32 V-cycle 2e-5 relative to the float64 oracle (unit roundoff 6e-8 times the
+work per row and the levels); FCG with the float32 V-cycle must still reach 1e-8 with at
+most three more iterations than the oracle's float64 run.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1810_04221_gb300 import problems as P
+from tests.gpu_util import csr_dev, dev, host
+
+pytestmark = pytest.mark.gpu
+B = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global B
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_04221_gb300 import binding, build
+    build.build()
+    binding.load()
+    B = binding
+    yield
+
+
+CASES = [
+    ("poisson3d_24_s3", lambda: P.poisson3d(24), 3, 20),
+    ("lognormal_16_s3", lambda: P.lognormal_diffusion(16, seed=3), 3, 30),
+    ("rand_s2", lambda: P.random_spd(6000, 7.0, seed=21), 2, 40),
+]
+
+
+def _vcycle_pair(mat, sweeps, cmax, prm_kw, pre=1, post=1, seed=0):
+    n = len(mat[0]) - 1
+    v = np.ones(n)
+    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax, pre=pre, post=post)
+    prm = B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, pre_sweeps=pre, post_sweeps=post, **prm_kw)
+    h = B.amg_setup(*csr_dev(*mat), dev(v), prm)
+    r = np.random.default_rng(seed).standard_normal(n)
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    got = host(B.amg_vcycle(h, dev(r), w))
+    h.free()
+    return got, H.vcycle(r)
+
+
+@pytest.mark.parametrize("tail_rows", [-1, 0, 1_000_000])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_vcycle_tail_settings(case, tail_rows):
+    name, gen, sweeps, cmax = case
+    got, ref = _vcycle_pair(gen(), sweeps, cmax, dict(tail_rows=tail_rows))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("pre,post", [(2, 1), (1, 2), (0, 1), (2, 3)])
+@pytest.mark.parametrize("tail_rows", [-1, 1_000_000])
+def test_vcycle_sweep_counts(pre, post, tail_rows):
+    got, ref = _vcycle_pair(P.poisson3d(20), 3, 20, dict(tail_rows=tail_rows), pre=pre, post=post)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_coarsest_above_dense_limit():
+    """A coarsest level larger than the dense-operator limit (2048 rows) runs its sweeps."""
+    mat = P.poisson2d(80)  # 6400 rows; coarse_max large keeps it a single level
+    got, ref = _vcycle_pair(mat, 2, 10_000, dict(tail_rows=-1))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("tail_rows", [-1, 0])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_vcycle_fp32(case, tail_rows):
+    name, gen, sweeps, cmax = case
+    got, ref = _vcycle_pair(gen(), sweeps, cmax, dict(vcycle_fp32=1, tail_rows=tail_rows))
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_pcg_fp32_vcycle(case):
+    name, gen, sweeps, cmax = case
+    mat = gen()
+    n = len(mat[0]) - 1
+    v = np.ones(n)
+    xs, b = P.manufactured_rhs(*mat, seed=5)
+    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax)
+    xr, st_r, it_r, _, _ = H.pcg(b, rtol=1e-8, itmax=500)
+    h = B.amg_setup(*csr_dev(*mat), dev(v), B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax,
+                                                                vcycle_fp32=1))
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8, itmax=500)
+    h.free()
+    assert st == B.AMG_OK and st_r == oracle.OK
+    assert it_r - 1 <= info["iters"] <= it_r + 3
+    assert info["rel_res_true"] <= 2e-8
+    assert np.abs(host(x) - xr).max() <= 1e-6 * np.abs(xr).max()

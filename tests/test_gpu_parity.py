@@ -314,3 +314,27 @@ def test_setup_deterministic():
     assert len(outs[0]) == len(outs[1])
     for (c1, v1), (c2, v2) in zip(*outs):
         assert np.array_equal(c1, c2) and bits_equal(v1, v2)
+
+
+def test_vcycle_barrier_wait_reports_timeout():
+    """The fused V-cycle tail waits at grid barriers with a bounded poll count.  With a
+    cap of one poll the waits give up: amg_vcycle reports AMG_ERR_TIMEOUT, and the
+    context stays usable for a normal hierarchy afterwards."""
+    n = 100
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    val = np.full(n, 2.0)
+    h = B.amg_setup(*csr_dev(rp, ci, val), dev(np.ones(n)), B.amg_default_params(loop_cap=1, coarse_max=0))
+    try:
+        w = torch.empty(n, dtype=torch.float64, device="cuda")
+        with pytest.raises(B.AmgError) as e:
+            B.amg_vcycle(h, dev(np.ones(n)), w)
+        assert e.value.status == B.AMG_ERR_TIMEOUT
+    finally:
+        h.free()
+    mat = P.poisson2d(16)
+    h = B.amg_setup(*csr_dev(*mat), dev(np.ones(256)))
+    x = torch.zeros(256, dtype=torch.float64, device="cuda")
+    st, info = B.amg_pcg_solve(h, dev(np.ones(256)), x)
+    assert st == B.AMG_OK
+    h.free()
