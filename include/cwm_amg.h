@@ -65,6 +65,11 @@ typedef struct {
                            as one cooperative launch per V-cycle; 0 = 65536, -1 = never
                            (default -1: on GB300 the grid barriers cost more than the
                            small launches they replace) */
+  double stall_ratio;   /* > 0: stop after a level whose coarsening ratio n_k / n_{k+1}
+                           is below this (the paper has no such rule; with strongly
+                           heterogeneous coefficients the pairwise matching can grow one
+                           aggregate into a hub and coarsen by a few rows per level);
+                           0 = off (default) */
 } amg_params;
 
 /* Statistics filled by amg_pcg_solve and amg_stats. */

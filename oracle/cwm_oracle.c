@@ -401,9 +401,10 @@ void or_free(or_hier *h) {
 }
 
 /* Build the hierarchy: levels while n_k > coarse_max and nl < max_levels; each level
- * does `sweeps` pairwise matching sweeps; stops early when a sweep forms no pair. */
+ * does `sweeps` pairwise matching sweeps; stops early when a sweep forms no pair, and,
+ * when stall_ratio > 0, after a level whose coarsening ratio n_k / n_{k+1} is below it. */
 or_hier *or_setup(int n, const int *rp, const int *ci, const double *val, const double *v,
-                  int sweeps, int coarse_max, int max_levels, int *status) {
+                  int sweeps, int coarse_max, int max_levels, double stall_ratio, int *status) {
   *status = OR_OK;
   if (n <= 0 || sweeps < 1 || sweeps > OR_MAX_SWEEPS || max_levels < 1 ||
       max_levels > OR_MAX_LEVELS || or_check_csr(n, rp, ci) != OR_OK) {
@@ -494,6 +495,7 @@ or_hier *or_setup(int n, const int *rp, const int *ci, const double *val, const 
     C->dl1 = l1_norms(&C->A);
     h->nl++;
     if (F->sweep_pairs[done_sweeps - 1] == 0 || done_sweeps < sweeps) break;
+    if (stall_ratio > 0.0 && (double)F->A.n < stall_ratio * (double)C->A.n) break;
   }
   if (*status != OR_OK) { or_free(h); return NULL; }
   return h;

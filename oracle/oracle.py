@@ -59,7 +59,7 @@ def _load():
             "or_prolongator": (i, [i, i, _i32p, _f64p, _f64p, _f64p]),
             "or_galerkin_nnz": (l, [i, _i32p, _i32p, _f64p, i, _i32p, _f64p]),
             "or_galerkin": (i, [i, _i32p, _i32p, _f64p, i, _i32p, _f64p, _i32p, _i32p, _f64p]),
-            "or_setup": (vp, [i, _i32p, _i32p, _f64p, _f64p, i, i, i, C.POINTER(i)]),
+            "or_setup": (vp, [i, _i32p, _i32p, _f64p, _f64p, i, i, i, d, C.POINTER(i)]),
             "or_set_cycle": (None, [vp, i, i, i]),
             "or_num_levels": (i, [vp]),
             "or_level_n": (i, [vp, i]),
@@ -171,13 +171,13 @@ class Hierarchy:
     """An oracle hierarchy (levels of A^k, composed P^k, smooth vectors)."""
 
     def __init__(self, rp, ci, val, v, sweeps=2, coarse_max=40, max_levels=40,
-                 pre=1, post=1, coarse_sweeps=20):
+                 pre=1, post=1, coarse_sweeps=20, stall_ratio=0.0):
         rp, ci, val = _csr(rp, ci, val)
         v = np.ascontiguousarray(v, dtype=np.float64)
         self._lib = _load()
         st = C.c_int(0)
         self._h = self._lib.or_setup(len(rp) - 1, rp, ci, val, v, sweeps, coarse_max,
-                                     max_levels, C.byref(st))
+                                     max_levels, float(stall_ratio), C.byref(st))
         if not self._h:
             raise ValueError(f"oracle setup failed with status {st.value}")
         self._lib.or_set_cycle(self._h, pre, post, coarse_sweeps)

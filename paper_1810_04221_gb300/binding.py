@@ -44,6 +44,7 @@ class AmgParams(C.Structure):
         ("trace", C.c_int),
         ("trace_filter", C.c_char * 32),
         ("tail_rows", C.c_int),
+        ("stall_ratio", C.c_double),
     ]
 
 

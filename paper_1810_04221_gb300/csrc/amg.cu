@@ -484,6 +484,7 @@ void amg_default_params(amg_params *p) {
   p->loop_cap = 0;
   p->trace = 0;
   p->tail_rows = -1;
+  p->stall_ratio = 0.0;
 }
 
 const char *amg_status_string(amg_status s) {
@@ -556,6 +557,8 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
     CWM_TRY(coarsen_level(h, &made));
     if (h->lev.size() == before) break;  // no pair at all: the current level is the coarsest
     if (!made) break;
+    const Level &Fl = h->lev[h->lev.size() - 2], &Cl = h->lev.back();
+    if (P.stall_ratio > 0.0 && (double)Fl.n < P.stall_ratio * (double)Cl.n) break;
   }
   for (Level &L : h->lev) CWM_TRY(finish_level(h, L));
   h->lev.back().nsweeps = 0;

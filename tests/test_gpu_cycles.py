@@ -98,3 +98,20 @@ def test_pcg_fp32_vcycle(case):
     assert it_r - 1 <= info["iters"] <= it_r + 3
     assert info["rel_res_true"] <= 2e-8
     assert np.abs(host(x) - xr).max() <= 1e-6 * np.abs(xr).max()
+
+
+def test_stall_ratio_hierarchy_matches_oracle():
+    """The optional stall-ratio stop gives the oracle's hierarchy, bit for bit."""
+    mat = P.lognormal_diffusion(24, seed=0)
+    n = len(mat[0]) - 1
+    H = oracle.Hierarchy(*mat, np.ones(n), sweeps=3, coarse_max=10, stall_ratio=1.2)
+    h = B.amg_setup(*csr_dev(*mat), dev(np.ones(n)),
+                    B.amg_default_params(sweeps_per_level=3, coarse_max=10, stall_ratio=1.2))
+    try:
+        assert B.amg_num_levels(h) == H.nl
+        for k in range(H.nl):
+            got, ref = B.amg_level_export(h, k), H.level(k)
+            assert np.array_equal(host(got["ci"]), ref["ci"])
+            assert np.array_equal(host(got["val"]).view(np.int64), ref["val"].view(np.int64))
+    finally:
+        h.free()

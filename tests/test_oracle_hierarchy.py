@@ -216,3 +216,17 @@ def test_hierarchy_rejects_bad_input():
     with pytest.raises(ValueError):  # zero diagonal
         oracle.Hierarchy(rp, np.array([0, 1, 0, 1], np.int32), np.array([0.0, -1, -1, 2]),
                          np.ones(2), coarse_max=1)
+
+
+def test_hierarchy_stall_ratio_stops_hub_growth():
+    """With strongly heterogeneous coefficients one aggregate can become a hub that all
+    remaining vertices touch (a star): each sweep then pairs one vertex.  The optional
+    stall ratio stops after the first level that coarsens by less than the ratio."""
+    mat = P.lognormal_diffusion(24, seed=0)
+    n = len(mat[0]) - 1
+    H = oracle.Hierarchy(*mat, np.ones(n), sweeps=3, coarse_max=10, max_levels=40)
+    ns = [H.level_n(k) for k in range(H.nl)]
+    H2 = oracle.Hierarchy(*mat, np.ones(n), sweeps=3, coarse_max=10, max_levels=40, stall_ratio=1.2)
+    ns2 = [H2.level_n(k) for k in range(H2.nl)]
+    k = next(i for i in range(1, len(ns)) if ns[i - 1] < 1.2 * ns[i])
+    assert ns2 == ns[:k + 1]
