@@ -70,6 +70,8 @@ typedef struct {
                            heterogeneous coefficients the pairwise matching can grow one
                            aggregate into a hub and coarsen by a few rows per level);
                            0 = off (default) */
+  int gamma;            /* coarse cycles per level: 1 = V-cycle (default), 2 = W-cycle
+                           (Sec. 5.1; its cost grows as 2^levels) */
 } amg_params;
 
 /* Statistics filled by amg_pcg_solve and amg_stats. */

@@ -376,6 +376,7 @@ typedef struct {
   int nl;
   or_level lev[OR_MAX_LEVELS];
   int pre, post, coarse;  /* l1-Jacobi sweeps */
+  int gamma;              /* recursive calls per level: 1 = V-cycle, 2 = W-cycle */
 } or_hier;
 
 static double *l1_norms(const or_csr *A) {
@@ -413,7 +414,7 @@ or_hier *or_setup(int n, const int *rp, const int *ci, const double *val, const 
   }
   or_hier *h = (or_hier *)xcalloc(1, sizeof(or_hier));
   if (!h) { *status = OR_ERR_OOM; return NULL; }
-  h->pre = 1; h->post = 1; h->coarse = 20;
+  h->pre = 1; h->post = 1; h->coarse = 20; h->gamma = 1;
   long nnz = rp[n];
   or_level *L0 = &h->lev[0];
   L0->A.n = n;
@@ -504,6 +505,8 @@ or_hier *or_setup(int n, const int *rp, const int *ci, const double *val, const 
 void or_set_cycle(or_hier *h, int pre, int post, int coarse) {
   h->pre = pre; h->post = post; h->coarse = coarse;
 }
+
+void or_set_gamma(or_hier *h, int gamma) { h->gamma = gamma; }
 int or_num_levels(const or_hier *h) { return h->nl; }
 int or_level_n(const or_hier *h, int k) { return h->lev[k].A.n; }
 long or_level_nnz(const or_hier *h, int k) { return h->lev[k].A.nnz; }
@@ -555,12 +558,15 @@ void or_l1_jacobi(const or_hier *h, int k, const double *b, double *x, int sweep
   free(tmp);
 }
 
-/* x^k = V-cycle(k, b^k) with x^k starting from zero. */
-static void vcycle(const or_hier *h, int k, const double *b, double *x) {
+/* One multigrid cycle on level k (Algorithm 1) from the starting guess in x: pre-smoothing,
+ * the coarse correction x += P x^{k+1} where x^{k+1} comes from gamma cycles on level k+1
+ * started from zero (gamma = 1: V-cycle; 2: W-cycle, the second cycle starting from the
+ * first one's result), and post-smoothing.  The coarsest level does `coarse` l1-Jacobi
+ * sweeps from the starting guess. */
+static void cycle(const or_hier *h, int k, const double *b, double *x) {
   const or_level *L = &h->lev[k];
   int n = L->A.n;
   double *tmp = (double *)xcalloc((size_t)n, sizeof(double));
-  memset(x, 0, sizeof(double) * (size_t)n);
   if (k == h->nl - 1) {
     for (int s = 0; s < h->coarse; ++s) l1_jacobi_sweep(&L->A, L->dl1, b, x, tmp);
     free(tmp);
@@ -573,12 +579,18 @@ static void vcycle(const or_hier *h, int k, const double *b, double *x) {
   double *xc = (double *)xcalloc((size_t)nc, sizeof(double));
   spmv(&L->A, x, tmp);
   for (int i = 0; i < n; ++i) bc[L->agg[i]] = bc[L->agg[i]] + L->p[i] * (b[i] - tmp[i]);
-  vcycle(h, k + 1, bc, xc);
+  for (int g = 0; g < h->gamma; ++g) cycle(h, k + 1, bc, xc);
   for (int i = 0; i < n; ++i) x[i] = x[i] + L->p[i] * xc[L->agg[i]];
   for (int s = 0; s < h->post; ++s) l1_jacobi_sweep(&L->A, L->dl1, b, x, tmp);
   free(bc);
   free(xc);
   free(tmp);
+}
+
+/* x^k = cycle(k, b^k) with x^k starting from zero. */
+static void vcycle(const or_hier *h, int k, const double *b, double *x) {
+  memset(x, 0, sizeof(double) * (size_t)h->lev[k].A.n);
+  cycle(h, k, b, x);
 }
 
 void or_vcycle(const or_hier *h, const double *r, double *w) { vcycle(h, 0, r, w); }

@@ -61,6 +61,7 @@ def _load():
             "or_galerkin": (i, [i, _i32p, _i32p, _f64p, i, _i32p, _f64p, _i32p, _i32p, _f64p]),
             "or_setup": (vp, [i, _i32p, _i32p, _f64p, _f64p, i, i, i, d, C.POINTER(i)]),
             "or_set_cycle": (None, [vp, i, i, i]),
+            "or_set_gamma": (None, [vp, i]),
             "or_num_levels": (i, [vp]),
             "or_level_n": (i, [vp, i]),
             "or_level_nnz": (l, [vp, i]),
@@ -171,7 +172,7 @@ class Hierarchy:
     """An oracle hierarchy (levels of A^k, composed P^k, smooth vectors)."""
 
     def __init__(self, rp, ci, val, v, sweeps=2, coarse_max=40, max_levels=40,
-                 pre=1, post=1, coarse_sweeps=20, stall_ratio=0.0):
+                 pre=1, post=1, coarse_sweeps=20, stall_ratio=0.0, gamma=1):
         rp, ci, val = _csr(rp, ci, val)
         v = np.ascontiguousarray(v, dtype=np.float64)
         self._lib = _load()
@@ -181,6 +182,7 @@ class Hierarchy:
         if not self._h:
             raise ValueError(f"oracle setup failed with status {st.value}")
         self._lib.or_set_cycle(self._h, pre, post, coarse_sweeps)
+        self._lib.or_set_gamma(self._h, gamma)
 
     def close(self):
         if self._h:

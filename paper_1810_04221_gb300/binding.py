@@ -45,6 +45,7 @@ class AmgParams(C.Structure):
         ("trace_filter", C.c_char * 32),
         ("tail_rows", C.c_int),
         ("stall_ratio", C.c_double),
+        ("gamma", C.c_int),
     ]
 
 

@@ -395,19 +395,49 @@ void fill_tail(amg_hierarchy *h, int k0, TailArgs<V> &a) {
 
 // x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
 template <class V>
+amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init);
+
+// x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
+template <class V>
 amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
+  return cycle_level<V>(h, k, b, x, true);
+}
+
+// One cycle on level k from the starting guess in x (zero_init: x = 0, not read).  The
+// coarse correction runs `gamma` cycles on level k+1 (1: V-cycle; 2: W-cycle, Sec. 5.1), the
+// first from zero and the others from the previous result.  A starting guess other than
+// zero only occurs on levels k >= 1, where x is the level's own vector.
+template <class V>
+amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init) {
   using LV = LevelVec<V>;
   cudaStream_t s = h->stream;
   Level &L = h->lev[k];
   LevelTag tag(k);
-  if (k == h->tail_start)
+  const int gamma = h->prm.gamma < 1 ? 1 : h->prm.gamma;
+  if (k == h->tail_start && zero_init && gamma == 1)
     return vcycle_tail<V>(tail_args<V>(h), tail_dev_args<V>(h), b, x, h->bar.get(), h->err.get(), s);
   const CsrView<V> A = LV::A(L);
   const V *dinv = LV::dinv(L);
   V *t1 = LV::t1(L), *t2 = LV::t2(L);
   const int nl = (int)h->lev.size();
-  if (k == nl - 1) {  // coarsest: l1-Jacobi sweeps from zero
+  if (k == nl - 1) {  // coarsest: l1-Jacobi sweeps from the starting guess
     const int sweeps = h->prm.coarse_sweeps;
+    if (!zero_init) {
+      if (sweeps <= 0) return AMG_OK;
+      if (LV::dense(L)) {  // x += B (b - A x) with B the dense operator of the sweeps
+        CWM_TRY(residual_t<V>(A, b, x, t1, s));
+        CWM_TRY(dense_coarse_apply<V>(A.n, LV::dense(L), t1, t2, s));
+        return add_to<V>(A.n, t2, x, s);
+      }
+      const V *cur = x;
+      for (int i = 0; i < sweeps; ++i) {
+        V *dst = cur == t1 ? t2 : t1;
+        CWM_TRY(jacobi<V>(A, dinv, b, cur, dst, s));
+        cur = dst;
+      }
+      CWM_CUDA(cudaMemcpyAsync(x, cur, sizeof(V) * (size_t)A.n, cudaMemcpyDeviceToDevice, s));
+      return AMG_OK;
+    }
     if (LV::dense(L)) return dense_coarse_apply<V>(A.n, LV::dense(L), b, x, s);
     if (A.n <= kCoarseBlockMax) return coarse_solve_block<V>(A, dinv, b, x, sweeps, s);
     if (sweeps <= 0) { CWM_CUDA(cudaMemsetAsync(x, 0, sizeof(V) * (size_t)A.n, s)); return AMG_OK; }
@@ -420,18 +450,18 @@ amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
     }
     return AMG_OK;
   }
-  // pre-smoothing from zero: the first sweep is x = D^{-1} b
-  const V *xs = nullptr;
+  // pre-smoothing; from zero the first sweep is x = D^{-1} b
+  const V *xs = zero_init ? nullptr : x;
   for (int i = 0; i < h->prm.pre_sweeps; ++i) {
     V *dst = (xs == t1) ? t2 : t1;
-    if (i == 0) CWM_TRY(scale<V>(A.n, dinv, b, dst, s));
+    if (i == 0 && zero_init) CWM_TRY(scale<V>(A.n, dinv, b, dst, s));
     else CWM_TRY(jacobi<V>(A, dinv, b, xs, dst, s));
     xs = dst;
   }
   Level &C = h->lev[k + 1];
   V *rtmp = (xs == t1) ? t2 : t1;  // free until the prolongation writes it
   CWM_TRY(resid_restrict_rb<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, rtmp, LV::b(C), s));
-  CWM_TRY(vcycle_level<V>(h, k + 1, LV::b(C), LV::x(C)));
+  for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C), LV::x(C), g == 0));
   V *y = (xs == t1) ? t2 : t1;
   CWM_TRY(prolong<V>(A.n, L.agg.get(), LV::p(L), LV::x(C), xs, y, s));
   const int post = h->prm.post_sweeps;
@@ -485,6 +515,7 @@ void amg_default_params(amg_params *p) {
   p->trace = 0;
   p->tail_rows = -1;
   p->stall_ratio = 0.0;
+  p->gamma = 1;
 }
 
 const char *amg_status_string(amg_status s) {

@@ -273,6 +273,30 @@ __global__ void __launch_bounds__(kRB) k_resid_rb(int n, const int *__restrict__
   if (threadIdx.x < nrows) r[i] = b[i] - dot;
 }
 
+template <class V>
+amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s) {
+  if (A.n == 0) return AMG_OK;
+  CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
+  k_resid_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+template <class V>
+__global__ void k_add_to(int n, const V *__restrict__ x, V *__restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+template <class V>
+amg_status add_to(int n, const V *x, V *y, cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  CWM_TRACE("add", 3.0 * sizeof(V) * n, s);
+  k_add_to<V><<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, x, y);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
 // bc[I] = sum over the members m of I (ascending) of p_m r_m
 template <class V>
 __global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__restrict__ mlist,
@@ -857,7 +881,9 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
   template amg_status resid_restrict_rb<V>(const CsrView<V> &, int, const int *, const int *, const V *,     \
                                            const V *, const V *, V *, V *, cudaStream_t);                    \
   template amg_status coarse_solve_block<V>(const CsrView<V> &, const V *, const V *, V *, int, cudaStream_t); \
-  template amg_status dense_coarse_apply<V>(int, const V *, const V *, V *, cudaStream_t);
+  template amg_status dense_coarse_apply<V>(int, const V *, const V *, V *, cudaStream_t);                  \
+  template amg_status residual_t<V>(const CsrView<V> &, const V *, const V *, V *, cudaStream_t);          \
+  template amg_status add_to<V>(int, const V *, V *, cudaStream_t);
 CWM_INST(double)
 CWM_INST(float)
 

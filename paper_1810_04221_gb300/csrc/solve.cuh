@@ -42,6 +42,12 @@ amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t 
 template <class V>
 amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                              const V *b, const V *x, V *r_scratch, V *bc, cudaStream_t s);
+// r = b - A x (any value type)
+template <class V>
+amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s);
+// y += x
+template <class V>
+amg_status add_to(int n, const V *x, V *y, cudaStream_t s);
 // y = x + p .* xc[agg]; x may be NULL (0)
 template <class V>
 amg_status prolong(int n, const int *agg, const V *p, const V *xc, const V *x, V *y, cudaStream_t s);

@@ -115,3 +115,31 @@ def test_stall_ratio_hierarchy_matches_oracle():
             assert np.array_equal(host(got["val"]).view(np.int64), ref["val"].view(np.int64))
     finally:
         h.free()
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("gen,sweeps,cmax", [(lambda: P.poisson3d(24), 3, 20),
+                                             (lambda: P.random_spd(5000, 6.0, seed=31), 2, 60)])
+def test_wcycle_matches_oracle(gen, sweeps, cmax, fp32):
+    """W-cycle (gamma = 2, Sec. 5.1): the second coarse cycle starts from the first one's
+    result, on the GPU as in the oracle."""
+    mat = gen()
+    n = len(mat[0]) - 1
+    v = np.ones(n)
+    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax, gamma=2)
+    h = B.amg_setup(*csr_dev(*mat), dev(v), B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, gamma=2,
+                                                                vcycle_fp32=fp32))
+    try:
+        r = np.random.default_rng(2).standard_normal(n)
+        w = torch.empty(n, dtype=torch.float64, device="cuda")
+        got = host(B.amg_vcycle(h, dev(r), w))
+        ref = H.vcycle(r)
+        assert np.abs(got - ref).max() <= (2e-5 if fp32 else 1e-12) * np.abs(ref).max()
+        xs, b = P.manufactured_rhs(*mat, seed=4)
+        xr, st_r, it_r, _, _ = H.pcg(b, rtol=1e-8, itmax=300)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8, itmax=300)
+        assert st == B.AMG_OK and st_r == oracle.OK
+        assert it_r - 1 <= info["iters"] <= it_r + (3 if fp32 else 1)
+    finally:
+        h.free()

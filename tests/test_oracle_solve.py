@@ -145,3 +145,43 @@ def test_fcg_poisson64_reference_iterations():
     assert st == oracle.OK and 5 < it < 60
     assert abs(rr - rt) < 1e-10
     assert np.abs(x - xs).max() < 1e-5
+
+
+@pytest.mark.parametrize("kind", ["diff", "p2"])
+def test_wcycle_error_propagation_identity(kind):
+    """W-cycle (two coarse cycles per level, Sec. 5.1): E_k = S^post (I - P (I - E_{k+1}^2)
+    A_{k+1}^{-1} P^T A_k) S^pre, with E the error propagator I - B A of each level and
+    E_coarsest = (I - D^-1 A)^sweeps."""
+    _, H = _hier(kind, gamma=2)
+    A, Pm, D = _dense_levels(H)
+    nl = H.nl
+    assert nl >= 3
+    E = [None] * nl
+    nc = A[-1].shape[0]
+    E[-1] = np.linalg.matrix_power(np.eye(nc) - A[-1] / D[-1][:, None], 20)
+    for k in range(nl - 2, -1, -1):
+        n = A[k].shape[0]
+        S = np.eye(n) - A[k] / D[k][:, None]
+        Ec2 = E[k + 1] @ E[k + 1]
+        Bc = (np.eye(A[k + 1].shape[0]) - Ec2) @ np.linalg.inv(A[k + 1])
+        C = np.eye(n) - Pm[k] @ Bc @ Pm[k].T @ A[k]
+        E[k] = S @ C @ S
+    B0 = (np.eye(A[0].shape[0]) - E[0]) @ np.linalg.inv(A[0])
+    r = np.random.default_rng(8).standard_normal(A[0].shape[0])
+    w = H.vcycle(r)
+    ref = B0 @ r
+    assert np.abs(w - ref).max() <= 1e-10 * np.abs(ref).max()
+    # the W-cycle is symmetric too
+    y = np.random.default_rng(9).standard_normal(A[0].shape[0])
+    assert abs(H.vcycle(r) @ y - r @ H.vcycle(y)) <= 1e-12 * abs(r @ H.vcycle(y)) + 1e-14
+
+
+def test_wcycle_fewer_iterations_than_vcycle():
+    """Sec. 5.1: the W-cycle needs fewer FCG iterations than the V-cycle.  (Its cost grows
+    as 2^levels, so the hierarchy here is kept short.)"""
+    rp, ci, val = P.poisson3d(16)
+    n = len(rp) - 1
+    xs, b = P.manufactured_rhs(rp, ci, val, seed=1)
+    itv = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=3, coarse_max=10).pcg(b, rtol=1e-8)[2]
+    itw = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=3, coarse_max=10, gamma=2).pcg(b, rtol=1e-8)[2]
+    assert itw < itv
