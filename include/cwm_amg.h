@@ -203,6 +203,17 @@ amg_status cwm_galerkin(int n, const int32_t *d_row_ptr, const int32_t *d_col, c
                         int32_t *d_colc, double *d_valc, int64_t capacity, int64_t *h_nnzc,
                         void *stream);
 
+/* ---- Differentiation of a solve x = A^{-1} b ---- */
+
+/* The sampled outer product on the pattern of A: d_out[k] = alpha * (lambda_i * x_j) for
+ * every stored slot k = (i, j).  With lambda = A^{-1} dL/dx (the adjoint solve, A symmetric)
+ * and alpha = -1 this is dL/dA_ij of a loss L(x) (Sec. 1: A x = b; the differentiation is an
+ * extension of the paper's solver).  d_lambda, d_x: device, n doubles; d_out: device, nnz
+ * doubles.  Errors: INVALID_ARG.  Asynchronous on stream. */
+amg_status cwm_pattern_outer(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
+                             const double *d_lambda, const double *d_x, double alpha, double *d_out,
+                             void *stream);
+
 /* ---- Tracing: per kernel class, CUDA events recorded on the launching stream ---- */
 
 /* One kernel class ("jacobi@0" = the l1-Jacobi kernel on level 0): launches, summed

@@ -25,7 +25,7 @@ EXPORTS = (
     "amg_num_levels", "amg_level_info", "amg_level_export", "amg_sweep_mate", "cwm_edge_weights",
     "cwm_suitor_match", "cwm_aggregate", "cwm_galerkin", "amg_status_string", "amg_last_error",
     "amg_trace_enable", "amg_trace_reset", "amg_trace_count", "amg_trace_get", "amg_launch_count",
-    "cwm_suitor_match_noalloc",
+    "cwm_suitor_match_noalloc", "cwm_pattern_outer",
 )
 
 
@@ -105,6 +105,7 @@ def load(path: str | None = None):
             "cwm_edge_weights": (i, [i, i64, vp, vp, vp, vp, vp, vp]),
             "cwm_suitor_match": (i, [i, i64, vp, vp, vp, vp, vp]),
             "cwm_suitor_match_noalloc": (i, [i, i64, vp, vp, vp, vp, vp]),
+            "cwm_pattern_outer": (i, [i, i64, vp, vp, vp, vp, d, vp, vp]),
             "cwm_aggregate": (i, [i, vp, vp, vp, vp, vp, ip, ip, vp]),
             "cwm_galerkin": (i, [i, vp, vp, vp, i, vp, vp, vp, vp, vp, i64, C.POINTER(i64), vp]),
             "amg_trace_enable": (i, [vp, i, C.c_char_p]),
@@ -343,3 +344,14 @@ def amg_trace(h: AmgHandle) -> list[dict]:
 
 def amg_launch_count() -> int:
     return int(load().amg_launch_count())
+
+
+def cwm_pattern_outer(row_ptr, col, lam, x, alpha: float = 1.0, out=None, stream=None):
+    """out[k] = alpha * lam[i] * x[j] on the stored pattern (i, j) of A."""
+    n, nnz = row_ptr.numel() - 1, col.numel()
+    if out is None:
+        out = torch.empty(nnz, dtype=torch.float64, device=x.device)
+    _check(load().cwm_pattern_outer(n, nnz, _dev(row_ptr, torch.int32, "row_ptr"), _dev(col, torch.int32, "col"),
+                                    _dev(lam, torch.float64, "lam", n), _dev(x, torch.float64, "x", n), float(alpha),
+                                    _dev(out, torch.float64, "out", nnz), _stream(stream)), "cwm_pattern_outer")
+    return out

@@ -227,3 +227,62 @@ def manufactured_rhs(rp, ci, val, seed: int = 0):
 def to_scipy(rp, ci, val) -> sp.csr_matrix:
     n = len(rp) - 1
     return sp.csr_matrix((val, ci, rp), shape=(n, n))
+
+
+_FV_PATTERN_CACHE: dict = {}
+
+
+def _fv_pattern(shape):
+    """COO (rows, cols) of diffusion_fv's entries in its assembly order, the permutation that
+    sorts them into CSR order, and the CSR (row_ptr, col)."""
+    if shape in _FV_PATTERN_CACHE:
+        return _FV_PATTERN_CACHE[shape]
+    mz, my, mx = shape
+    n = mz * my * mx
+    idx = np.arange(n, dtype=np.int64).reshape(mz, my, mx)
+    rows, cols = [], []
+    for axis in (2, 1, 0):
+        i0 = np.moveaxis(idx, axis, 0)
+        a, b = i0[:-1].ravel(), i0[1:].ravel()
+        rows += [a, b]
+        cols += [b, a]
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    perm = np.lexsort((c, r))
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(r, minlength=n), out=rp[1:])
+    out = (perm, rp.astype(np.int32), c[perm].astype(np.int32))
+    _FV_PATTERN_CACHE[shape] = out
+    return out
+
+
+def diffusion_fv_torch(kappa):
+    """diffusion_fv as differentiable torch operations: returns (row_ptr, col, val) with
+    row_ptr/col as numpy int32 and val a torch tensor on kappa's device and dtype, equal
+    value for value to diffusion_fv(kappa) (the same operations in the same order)."""
+    import torch
+    mz, my, mx = kappa.shape
+    perm, rp, ci = _fv_pattern((mz, my, mx))
+    diag = torch.zeros_like(kappa)
+    vals = []
+    for axis in (2, 1, 0):
+        k0 = kappa.movedim(axis, 0)
+        d0 = diag.movedim(axis, 0)
+        t = 2.0 * k0[:-1] * k0[1:] / (k0[:-1] + k0[1:])
+        zero = torch.zeros_like(k0[:1])
+        d0 = d0 + torch.cat([t, zero], 0)
+        d0 = d0 + torch.cat([zero, t], 0)
+        first = torch.zeros_like(k0)
+        first[0] = 1.0
+        last = torch.zeros_like(k0)
+        last[-1] = 1.0
+        d0 = d0 + first * (2.0 * k0)
+        d0 = d0 + last * (2.0 * k0)
+        diag = d0.movedim(0, axis)
+        tv = (-t).reshape(-1)
+        vals += [tv, tv]
+    vals.append(diag.reshape(-1))
+    coo = torch.cat(vals)
+    return rp, ci, coo[torch.as_tensor(perm, device=coo.device)]

@@ -324,7 +324,8 @@ def test_vcycle_barrier_wait_reports_timeout():
     rp = np.arange(n + 1, dtype=np.int32)
     ci = np.arange(n, dtype=np.int32)
     val = np.full(n, 2.0)
-    h = B.amg_setup(*csr_dev(rp, ci, val), dev(np.ones(n)), B.amg_default_params(loop_cap=1, coarse_max=0))
+    h = B.amg_setup(*csr_dev(rp, ci, val), dev(np.ones(n)),
+                    B.amg_default_params(loop_cap=1, coarse_max=0, tail_rows=0))
     try:
         w = torch.empty(n, dtype=torch.float64, device="cuda")
         with pytest.raises(B.AmgError) as e:

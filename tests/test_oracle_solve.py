@@ -185,3 +185,37 @@ def test_wcycle_fewer_iterations_than_vcycle():
     itv = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=3, coarse_max=10).pcg(b, rtol=1e-8)[2]
     itw = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=3, coarse_max=10, gamma=2).pcg(b, rtol=1e-8)[2]
     assert itw < itv
+
+
+def test_dense_solve_gradient_vs_finite_differences():
+    """dL/db = lambda and dL/dA_ij = -lambda_i x_j (oracle/gradient.py) against central
+    differences of the dense solve, each entry of A perturbed on its own."""
+    from oracle.gradient import solve_grad
+    rng = np.random.default_rng(3)
+    rp, ci, val = P.random_spd(30, 4.0, seed=8)
+    A = P.to_scipy(rp, ci, val).toarray()
+    b = rng.standard_normal(30)
+    xt = rng.standard_normal(30)
+    x, L, gb, gA = solve_grad(A, b, xt)
+    h = 1e-6
+    for i in rng.choice(30, 5, replace=False):
+        e = np.zeros(30)
+        e[i] = h
+        fd = (solve_grad(A, b + e, xt)[1] - solve_grad(A, b - e, xt)[1]) / (2 * h)
+        assert abs(fd - gb[i]) <= 1e-6 * max(1.0, abs(gb[i]))
+    for k in rng.choice(len(ci), 8, replace=False):
+        i = int(np.searchsorted(rp, k, side="right") - 1)
+        j = int(ci[k])
+        E = np.zeros_like(A)
+        E[i, j] = h
+        fd = (solve_grad(A + E, b, xt)[1] - solve_grad(A - E, b, xt)[1]) / (2 * h)
+        assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))
+
+
+def test_diffusion_fv_torch_matches_numpy():
+    import torch
+    k = P.lognormal_kappa(6, seed=2)
+    rp, ci, val = P.diffusion_fv(k)
+    rp2, ci2, v2 = P.diffusion_fv_torch(torch.from_numpy(k))
+    assert np.array_equal(rp, rp2) and np.array_equal(ci, ci2)
+    assert np.array_equal(val.view(np.int64), v2.numpy().view(np.int64))
