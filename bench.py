@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 
 def workload(name: str):
-    """(description dict, (rp, ci, val), v, b, x*, sweeps, coarse_max, fp32)."""
+    """(description, (rp, ci, val), v, b, x*, sweeps, coarse_max, fp32, extra params)."""
     if name == "poisson3d_128":
         mat = P.poisson3d(128)
         n = len(mat[0]) - 1
@@ -58,7 +58,8 @@ def workload(name: str):
         n = len(mat[0]) - 1
         v = np.ones(n)
         sweeps, cmax, fp32 = 3, 1000, True
-        desc = "3D FV diffusion 160^3, log-kappa N(0,4), 3 sweeps/level, coarse<=1000, FP32 V-cycle in FP64 FCG"
+        desc = ("3D FV diffusion 160^3, log-kappa N(0,4), 3 sweeps/level, coarse<=1000, stall ratio 1.2, "
+                "FP32 V-cycle in FP64 FCG")
     elif name == "elasticity_64":
         mat = P.elasticity_q1(64)
         n = len(mat[0]) - 1
@@ -67,8 +68,9 @@ def workload(name: str):
         desc = "3D Q1 elasticity 64^3 nodes, x=0 clamped, 2 sweeps/level, coarse<=1000, FP32 V-cycle in FP64 FCG"
     else:
         raise SystemExit(f"unknown workload {name}")
+    extra = {"stall_ratio": 1.2} if name == "lognormal_160" else {}
     xs, b = P.manufactured_rhs(*mat, seed=0)
-    return desc, mat, v, b, xs, sweeps, cmax, fp32
+    return desc, mat, v, b, xs, sweeps, cmax, fp32, extra
 
 
 # --------------------------------------------------------------------- helpers ----
@@ -168,7 +170,7 @@ def run_cuda(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     B.load()
-    desc, mat, v, b, xs, sweeps, cmax, fp32 = workload(args.workload)
+    desc, mat, v, b, xs, sweeps, cmax, fp32, extra = workload(args.workload)
     if args.fp32 is not None:
         fp32 = bool(args.fp32)
     rp, ci, val = mat
@@ -180,7 +182,7 @@ def run_cuda(args, rank, world, dist):
 
     def params(trace=0, filt=""):
         return B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, vcycle_fp32=int(fp32), trace=trace,
-                                    trace_filter=filt, check_input=0)
+                                    trace_filter=filt, check_input=0, **extra)
 
     def step(prm, evs=None):
         if evs:
@@ -195,13 +197,14 @@ def run_cuda(args, rank, world, dist):
         return h, st, info
 
     # warm-up; the first one traces every kernel class to find the dominant one
-    dominant, trace_all = None, []
+    dominant, trace_all, level_sizes = None, [], []
     for w in range(max(args.warmup, 1)):
         h, st, info = step(params(trace=1 if w == 0 else 0))
         if w == 0:
             trace_all = B.amg_trace(h)
             if trace_all:
                 dominant = max(trace_all, key=lambda e: e["total_ms"])["name"]
+            level_sizes = [list(B.amg_level_info(h, k)[:2]) for k in range(B.amg_num_levels(h))]
         h.free()
     torch.cuda.synchronize()
 
@@ -286,7 +289,7 @@ def run_cuda(args, rank, world, dist):
     variant = None
     if args.variant and dist is None:
         prm32 = B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, vcycle_fp32=int(not fp32),
-                                     check_input=0)
+                                     check_input=0, **extra)
         res = []
         for _ in range(3):
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -303,7 +306,7 @@ def run_cuda(args, rank, world, dist):
     # CPU baseline: the oracle as it stands, one full step, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(mat, v, b, sweeps, cmax, args.rtol, args.itmax)
+        cpu = cpu_baseline(mat, v, b, sweeps, cmax, args.rtol, args.itmax, extra.get("stall_ratio", 0.0))
 
     last = infos[-1]
     out = {
@@ -318,6 +321,7 @@ def run_cuda(args, rank, world, dist):
         "setup_ms": round(statistics.median(setup_ms), 3), "solve_ms": round(statistics.median(solve_ms), 3),
         "iters": last["iters"], "ms_per_iter": round(statistics.median(solve_ms) / max(last["iters"], 1), 4),
         "levels": last["nl"], "vcmplx": round(last["vcmplx"], 4), "cratio": round(last["cratio"], 4),
+        "level_sizes": level_sizes,
         "rel_res_true": last["rel_res_true"], "err_vs_xstar": err,
         "status": [B.status_name(s) for s in statuses][-1],
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -331,10 +335,10 @@ def run_cuda(args, rank, world, dist):
         print(json.dumps(out))
 
 
-def cpu_baseline(mat, v, b, sweeps, cmax, rtol, itmax):
+def cpu_baseline(mat, v, b, sweeps, cmax, rtol, itmax, stall_ratio=0.0):
     import oracle
     t0 = time.perf_counter()
-    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax)
+    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax, stall_ratio=stall_ratio)
     t1 = time.perf_counter()
     _, st, it, _, _ = H.pcg(b, rtol=rtol, itmax=itmax)
     t2 = time.perf_counter()
@@ -352,7 +356,7 @@ def run_reference(args, rank, world):
         return
     import oracle
     oracle.build()
-    desc, mat, v, b, xs, sweeps, cmax, fp32 = workload(args.workload)
+    desc, mat, v, b, xs, sweeps, cmax, fp32, extra = workload(args.workload)
     # warm-up on a small instance of the same problem family (pages code in)
     small = P.poisson3d(16)
     for _ in range(args.warmup):
@@ -362,7 +366,7 @@ def run_reference(args, rank, world):
     times, it = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax)
+        H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax, stall_ratio=extra.get("stall_ratio", 0.0))
         _, st, it, _, _ = H.pcg(b, rtol=args.rtol, itmax=args.itmax)
         times.append((time.perf_counter() - t0) * 1e3)
         H.close()

@@ -1,5 +1,6 @@
 // amg.cu -- the hierarchy driver (Sec. 2.1 setup, Sec. 5 parameters), the V-cycle
 // (Sec. 2.1, Algorithm 1), the flexible CG (Sec. 3.2, Algorithm 3) and the C ABI.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -637,7 +638,8 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   CWM_TRY(h->q.alloc(n, s));
   const int nb = fcg_partial_blocks(n);
   CWM_TRY(h->part.alloc(3 * (size_t)nb, s));
-  CWM_TRY(h->part2.alloc(nb, s));
+  // part2 takes the partial sums of sqnorm_partials and of fcg_update, whose grids differ
+  CWM_TRY(h->part2.alloc((size_t)std::max(nb, fcg_update_blocks(n)), s));
   CWM_TRY(h->scal.alloc(kFcgSlots, s));
   CWM_TRY(h->tick.alloc(4, s));
   CWM_CUDA(cudaMemsetAsync(h->tick.get(), 0, 4 * sizeof(unsigned), s));

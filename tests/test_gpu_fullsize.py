@@ -76,3 +76,18 @@ def test_poisson128_solve_vs_oracle(B, problem, fp32):
     xg = host(x)
     assert np.abs(xg - xr).max() <= 1e-6 * np.abs(xr).max()
     assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) < 1e-5
+
+
+def test_fcg_partial_sums_beyond_resident_grid(B):
+    """n = 3,375,000 (150^3): the FCG update grid (n / 2048 blocks) is larger than the
+    reduction grid (8 blocks per SM); both write their partial sums into buffers sized for
+    them.  The solve must converge like the oracle's at this size."""
+    mat = P.poisson3d(150)
+    n = len(mat[0]) - 1
+    xs, b = P.manufactured_rhs(*mat, seed=1)
+    h = B.amg_setup(*csr_dev(*mat), dev(np.ones(n)), B.amg_default_params(sweeps_per_level=3, coarse_max=1000))
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8)
+    h.free()
+    assert st == B.AMG_OK and info["rel_res_true"] <= 2e-8
+    assert np.linalg.norm(host(x) - xs) / np.linalg.norm(xs) < 1e-5
