@@ -35,7 +35,7 @@ from paper_1810_04221_gb300 import problems as P  # noqa: E402
 
 METRIC = "AMG setup ms + PCG solve ms to 1e-8 rel. residual"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")  # JSON text
 FALLBACK_HBM_GBS = 6800.0
 
 

@@ -99,6 +99,7 @@ struct amg_hierarchy {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [0]: iterations >= 1, [1]: the first
   std::vector<Tracer::Pending> gscopes[2];        // tracer scopes recorded inside each graph
+  long long gkernels[2] = {0, 0};                 // kernels in each graph (launch accounting)
   double *graph_x = nullptr;                      // the solution pointer the graphs use
   bool graphs_failed = false;
   // the fused coarse end of the V-cycle
@@ -817,7 +818,11 @@ void capture_graphs(amg_hierarchy *h, double *d_x) {
       break;
     }
     h->trace.capturing = true;
+    const long long before = launch_count();
     amg_status st = fcg_iteration(h, d_x, g);
+    // captured launches are not executed: take them back out and count them per replay
+    h->gkernels[g] = launch_count() - before;
+    count_launches(-h->gkernels[g]);
     h->trace.capturing = false;
     h->gscopes[g].swap(h->trace.graph_pending);
     h->trace.graph_pending.clear();
@@ -881,6 +886,7 @@ extern "C" amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x
     const int first = it == 0;
     if (h->gexec[first] && h->graph_x == d_x) {
       CWM_CUDA(cudaGraphLaunch(h->gexec[first], s));
+      count_launches(h->gkernels[first]);
       CWM_CUDA(cudaStreamSynchronize(s));
       if (h->trace.on) h->trace.collect(h->gscopes[first]);
     } else {

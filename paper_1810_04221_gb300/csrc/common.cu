@@ -43,6 +43,7 @@ amg_status status_from_device_bits(int bits, const char *where) {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 thread_local Tracer *g_tracer = nullptr;
 thread_local int g_trace_level = -1;

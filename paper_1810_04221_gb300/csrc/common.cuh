@@ -49,6 +49,8 @@ void count_launch();
     CWM_CUDA(cudaGetLastError()); \
   } while (0)
 long long launch_count();
+// Kernels launched by a replay of a captured graph (counted once per replay).
+void count_launches(long long k);
 
 // ---------------------------------------------------------------- tracing ----
 // Optional per-kernel-class timing with CUDA events recorded on the launching stream
