@@ -156,6 +156,16 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The largest `value` over all ranks (the job time of replicas); identity without dist."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------------- CUDA arm ----
 
 def run_cuda(args, rank, world, dist):
@@ -233,10 +243,7 @@ def run_cuda(args, rank, world, dist):
     total_ms = t_start.elapsed_time(t_end)
     setup_ms = [e[0].elapsed_time(e[1]) for e in evs]
     solve_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, device="cuda")
     ms_per_step = total_ms / args.steps
     err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
 

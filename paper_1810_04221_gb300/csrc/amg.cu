@@ -399,6 +399,9 @@ void fill_tail(amg_hierarchy *h, int k0, TailArgs<V> &a) {
 template <class V>
 amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init);
 
+// Largest level whose cycle uses the fused kernels (see cycle_level).
+constexpr int kFuseMaxRows = 300000;
+
 // x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
 template <class V>
 amg_status vcycle_level(amg_hierarchy *h, int k, const V *b, V *x) {
@@ -451,6 +454,16 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
       cur = dst;
     }
     return AMG_OK;
+  }
+  Level &C0 = h->lev[k + 1];
+  // The default cycle from zero (one pre- and one post-sweep) on a small level: the first
+  // sweep x = D^{-1} b is formed on the fly inside the residual and the coarse correction
+  // inside the post-sweep, two kernels fewer.  On large levels the extra gathers per
+  // nonzero cost more than the passes they save (measured), so they keep separate kernels.
+  if (zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= kFuseMaxRows) {
+    CWM_TRY(resid_scaled_restrict<V>(A, C0.n, L.mptr.get(), L.mlist.get(), LV::p(L), dinv, b, t1, LV::b(C0), s));
+    for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C0), LV::x(C0), g == 0));
+    return prolong_jacobi<V>(A, dinv, b, L.agg.get(), LV::p(L), LV::x(C0), x, s);
   }
   // pre-smoothing; from zero the first sweep is x = D^{-1} b
   const V *xs = zero_init ? nullptr : x;

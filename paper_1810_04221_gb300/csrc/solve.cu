@@ -86,6 +86,63 @@ __device__ __forceinline__ void rb_stage_rp(const int *__restrict__ rp, int r0, 
   __syncthreads();
 }
 
+// How the row dot reads its vector: X_PLAIN x_j; X_SCALED d_j x_j (the first l1-Jacobi sweep
+// from zero, x = D^{-1} b, formed on the fly); X_PROLONG d_j x_j + p_j xc[agg_j] (that sweep
+// plus the coarse correction, formed on the fly).
+enum XMode { X_PLAIN = 0, X_SCALED = 1, X_PROLONG = 2 };
+
+template <class V>
+struct XSrc {
+  const V *x;      // the vector (b for the scaled modes)
+  const V *d;      // D^{-1}
+  const V *p;      // P values
+  const int *agg;  // P columns
+  const V *xc;     // coarse correction
+};
+
+template <class V, int MODE>
+__device__ __forceinline__ V xval(const XSrc<V> &s, int j) {
+  if (MODE == X_PLAIN) return __ldg(s.x + j);
+  const V xs = __ldg(s.d + j) * __ldg(s.x + j);
+  if (MODE == X_SCALED) return xs;
+  return fma(__ldg(s.p + j), __ldg(s.xc + __ldg(s.agg + j)), xs);
+}
+
+// Row dot of row r0 + threadIdx.x with the vector described by xs (0 for threads beyond
+// nrows), same staging as rb_row_dot.
+template <class V, int MODE>
+__device__ __forceinline__ V rb_row_dot_x(const int *__restrict__ ci, const V *__restrict__ val, const XSrc<V> &xs,
+                                          int nrows, RowBlockSmem<V> &sm) {
+  const int t = threadIdx.x;
+  const int rs = sm.rp[0], re = sm.rp[nrows];
+  const int my_s = t < nrows ? sm.rp[t] : 0, my_e = t < nrows ? sm.rp[t + 1] : 0;
+  V acc = V(0);
+  for (int c0 = rs; c0 < re; c0 += kRBC) {
+    const int cend = min(c0 + kRBC, re);
+#pragma unroll
+    for (int e = 0; e < kRBE; ++e) {
+      const int k = c0 + e * kRB + t;
+      const bool in = k < cend;
+      sm.val[e * kRB + t] = in ? __ldcs(val + k) : V(0);
+      sm.col[e * kRB + t] = in ? __ldcs(ci + k) : 0;
+    }
+    __syncthreads();
+    const int lo = max(my_s, c0) - c0, hi = min(my_e, cend) - c0;
+    int k = lo;
+    for (; k + 4 <= hi; k += 4) {
+      const V x0 = xval<V, MODE>(xs, sm.col[k]), x1 = xval<V, MODE>(xs, sm.col[k + 1]);
+      const V x2 = xval<V, MODE>(xs, sm.col[k + 2]), x3 = xval<V, MODE>(xs, sm.col[k + 3]);
+      acc = fma(sm.val[k], x0, acc);
+      acc = fma(sm.val[k + 1], x1, acc);
+      acc = fma(sm.val[k + 2], x2, acc);
+      acc = fma(sm.val[k + 3], x3, acc);
+    }
+    for (; k < hi; ++k) acc = fma(sm.val[k], xval<V, MODE>(xs, sm.col[k]), acc);
+    __syncthreads();
+  }
+  return acc;
+}
+
 // Row dot of row r0 + threadIdx.x with x (0 for threads beyond nrows); ABS = sum of |a_ij|.
 template <class V, bool ABS>
 __device__ __forceinline__ V rb_row_dot(const int *__restrict__ ci, const V *__restrict__ val,
@@ -257,6 +314,90 @@ __global__ void __launch_bounds__(kBlock)
     }
     if (active && lane == 0) bc[I] = acc;
   }
+}
+
+template <class V>
+__global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__restrict__ mlist,
+                           const V *__restrict__ p, const V *__restrict__ r, V *__restrict__ bc);
+
+// r = b - A (D^{-1} b): the residual after the first l1-Jacobi sweep from zero, without
+// materialising that sweep
+template <class V>
+__global__ void __launch_bounds__(kRB) k_resid_scaled_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                         const V *__restrict__ val, const V *__restrict__ dinv,
+                                                         const V *__restrict__ b, V *__restrict__ r) {
+  __shared__ RowBlockSmem<V> sm;
+  const int r0 = blockIdx.x * kRB;
+  const int nrows = min(kRB, n - r0);
+  rb_stage_rp(rp, r0, nrows, sm.rp);
+  XSrc<V> xs{b, dinv, nullptr, nullptr, nullptr};
+  const V dot = rb_row_dot_x<V, X_SCALED>(ci, val, xs, nrows, sm);
+  const int i = r0 + threadIdx.x;
+  if (threadIdx.x < nrows) r[i] = b[i] - dot;
+}
+
+// x = y + D^{-1} (b - A y) with y = D^{-1} b + P xc formed on the fly: the coarse correction
+// of a V-cycle whose pre-smoothing was one sweep from zero, and one post-sweep
+template <class V>
+__global__ void __launch_bounds__(kRB) k_prolong_jacobi_rb(int n, const int *__restrict__ rp,
+                                                           const int *__restrict__ ci, const V *__restrict__ val,
+                                                           const V *__restrict__ dinv, const V *__restrict__ b,
+                                                           const int *__restrict__ agg, const V *__restrict__ p,
+                                                           const V *__restrict__ xc, V *__restrict__ x) {
+  __shared__ RowBlockSmem<V> sm;
+  const int r0 = blockIdx.x * kRB;
+  const int nrows = min(kRB, n - r0);
+  rb_stage_rp(rp, r0, nrows, sm.rp);
+  XSrc<V> xs{b, dinv, p, agg, xc};
+  const V dot = rb_row_dot_x<V, X_PROLONG>(ci, val, xs, nrows, sm);
+  const int i = r0 + threadIdx.x;
+  if (threadIdx.x < nrows) {
+    const V yi = fma(p[i], xc[agg[i]], dinv[i] * b[i]);
+    x[i] = yi + dinv[i] * (b[i] - dot);
+  }
+}
+
+// y = D^{-1} b + P xc
+template <class V>
+__global__ void k_prolong_scaled(int n, const int *__restrict__ agg, const V *__restrict__ p, const V *__restrict__ xc,
+                                 const V *__restrict__ dinv, const V *__restrict__ b, V *__restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(p[i], __ldg(xc + agg[i]), dinv[i] * b[i]);
+}
+
+template <class V>
+amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
+                                 const V *dinv, const V *b, V *r_scratch, V *bc, cudaStream_t s) {
+  if (nc == 0) return AMG_OK;
+  {
+    CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
+    k_resid_scaled_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, r_scratch);
+    CWM_LAUNCH();
+  }
+  CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
+  k_restrict<V><<<grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s>>>(nc, mptr, mlist, p, r_scratch, bc);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+template <class V>
+amg_status prolong_jacobi(const CsrView<V> &A, const V *dinv, const V *b, const int *agg, const V *p, const V *xc,
+                          V *x, cudaStream_t s) {
+  if (A.n == 0) return AMG_OK;
+  CWM_TRACE("prolong_jacobi", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + (5.0 * sizeof(V) + 4.0) * A.n, s);
+  k_prolong_jacobi_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, agg, p, xc, x);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+template <class V>
+amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const V *dinv, const V *b, V *y,
+                          cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  CWM_TRACE("prolong", (4.0 + 4.0 * sizeof(V)) * n, s);
+  k_prolong_scaled<V><<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, agg, p, xc, dinv, b, y);
+  CWM_LAUNCH();
+  return AMG_OK;
 }
 
 // r = b - A x (x may be NULL: r = b), row blocks
@@ -571,10 +712,15 @@ amg_status reciprocal(int n, const double *x, double *y, float *y32, cudaStream_
 }
 
 // ------------------------------------------------------------ FCG ----
-// blocks of the grid-stride FCG reductions: at most 8 resident blocks per SM
+// Blocks of the grid-stride FCG reductions: at most kDotsBlocksPerSm per SM, so that the
+// FP64 block reductions are paid once per several row blocks.
+#ifndef CWM_DOTS_BLOCKS_PER_SM
+#define CWM_DOTS_BLOCKS_PER_SM 12
+#endif
+constexpr int kDotsBlocksPerSm = CWM_DOTS_BLOCKS_PER_SM;
 int fcg_partial_blocks(int n) {
   const int rb = rb_grid(n > 0 ? n : 1);
-  const int cap = num_sms() * 8;
+  const int cap = num_sms() * kDotsBlocksPerSm;
   return rb < cap ? rb : cap;
 }
 constexpr int kUpdChunk = 8 * kRB;  // entries per fcg_update block
@@ -883,6 +1029,12 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
   template amg_status coarse_solve_block<V>(const CsrView<V> &, const V *, const V *, V *, int, cudaStream_t); \
   template amg_status dense_coarse_apply<V>(int, const V *, const V *, V *, cudaStream_t);                  \
   template amg_status residual_t<V>(const CsrView<V> &, const V *, const V *, V *, cudaStream_t);          \
+  template amg_status resid_scaled_restrict<V>(const CsrView<V> &, int, const int *, const int *, const V *,  \
+                                               const V *, const V *, V *, V *, cudaStream_t);               \
+  template amg_status prolong_jacobi<V>(const CsrView<V> &, const V *, const V *, const int *, const V *,    \
+                                        const V *, V *, cudaStream_t);                                       \
+  template amg_status prolong_scaled<V>(int, const int *, const V *, const V *, const V *, const V *, V *,    \
+                                        cudaStream_t);                                                       \
   template amg_status add_to<V>(int, const V *, V *, cudaStream_t);
 CWM_INST(double)
 CWM_INST(float)

@@ -42,6 +42,18 @@ amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t 
 template <class V>
 amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                              const V *b, const V *x, V *r_scratch, V *bc, cudaStream_t s);
+// r = b - A (D^{-1} b) into r_scratch, then bc = P^T r (the first sweep from zero fused in)
+template <class V>
+amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
+                                 const V *dinv, const V *b, V *r_scratch, V *bc, cudaStream_t s);
+// x = y + D^{-1}(b - A y) with y = D^{-1} b + P xc formed on the fly
+template <class V>
+amg_status prolong_jacobi(const CsrView<V> &A, const V *dinv, const V *b, const int *agg, const V *p, const V *xc,
+                          V *x, cudaStream_t s);
+// y = D^{-1} b + P xc
+template <class V>
+amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const V *dinv, const V *b, V *y,
+                          cudaStream_t s);
 // r = b - A x (any value type)
 template <class V>
 amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s);
