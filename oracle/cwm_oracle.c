@@ -33,6 +33,10 @@
  *     and adding left to right in ascending order of (min(i,j), max(i,j), i).  The order
  *     depends only on the unordered pair, so A_c is bit-symmetric when A is.  Every hit
  *     (I,J) is stored, structural zeros included; columns ascend.
+ *   - Single-precision Galerkin variant (the precision trade-off of Sec. 3.2 carried over
+ *     to the setup): for the levels chosen, p_i, p_j and a_ij are rounded to binary32, the
+ *     term is (p_i*p_j)*a_ij in binary32, and each entry sums its terms in binary32 from
+ *     +0.0 in the same order; the entry is then stored as the double of that float.
  *   - Several sweeps per level (Sec. 2.2, Sec. 5): sweep s matches the operator made by
  *     sweep s-1; the level prolongator is the composition of the sweeps' prolongators.
  *   - l1-Jacobi (Sec. 3.2): D_ii = sum_j |a_ij|; one sweep x <- x + (b - A x)/D.
@@ -273,7 +277,7 @@ int or_prolongator(int n, int nc, const int *agg, const double *v, double *p, do
 /* Sec. 2.1 / Sec. 3.1: Galerkin product A_c = P^T A P                         */
 /* ------------------------------------------------------------------------- */
 
-typedef struct { int I, J, kmin, kmax, i; double t; } or_term;
+typedef struct { int I, J, kmin, kmax, i; double t; float tf; } or_term;
 
 static int term_cmp(const void *x, const void *y) {
   const or_term *a = (const or_term *)x, *b = (const or_term *)y;
@@ -292,8 +296,9 @@ static void csr_free(or_csr *A) {
   A->rp = NULL; A->ci = NULL; A->val = NULL;
 }
 
-/* Builds Ac (allocated here) from A, agg and p.  Returns OR_OK or OR_ERR_OOM. */
-static int galerkin(const or_csr *A, int nc, const int *agg, const double *p, or_csr *Ac) {
+/* Builds Ac (allocated here) from A, agg and p; f32 != 0 forms and sums the terms in
+ * binary32.  Returns OR_OK or OR_ERR_OOM. */
+static int galerkin(const or_csr *A, int nc, const int *agg, const double *p, int f32, or_csr *Ac) {
   long m = A->nnz;
   or_term *T = (or_term *)xcalloc((size_t)m, sizeof(or_term));
   if (!T) return OR_ERR_OOM;
@@ -307,6 +312,11 @@ static int galerkin(const or_csr *A, int nc, const int *agg, const double *p, or
       T[q].kmax = i < j ? j : i;
       T[q].i = i;
       T[q].t = (p[i] * p[j]) * A->val[k];
+      {
+        const float pi = (float)p[i], pj = (float)p[j], a = (float)A->val[k];
+        const float pp = pi * pj;
+        T[q].tf = pp * a;
+      }
       ++q;
     }
   qsort(T, (size_t)m, sizeof(or_term), term_cmp);
@@ -320,14 +330,21 @@ static int galerkin(const or_csr *A, int nc, const int *agg, const double *p, or
   Ac->val = (double *)xcalloc((size_t)nnzc, sizeof(double));
   if (!Ac->rp || !Ac->ci || !Ac->val) { csr_free(Ac); free(T); return OR_ERR_OOM; }
   long out = -1;
+  float accf = 0.0f;
   for (long e = 0; e < m; ++e) {
     if (e == 0 || T[e].I != T[e - 1].I || T[e].J != T[e - 1].J) {
       ++out;
       Ac->ci[out] = T[e].J;
       Ac->val[out] = 0.0;
+      accf = 0.0f;
       Ac->rp[T[e].I + 1]++;
     }
-    Ac->val[out] = Ac->val[out] + T[e].t;
+    if (f32) {
+      accf = accf + T[e].tf;
+      Ac->val[out] = (double)accf;
+    } else {
+      Ac->val[out] = Ac->val[out] + T[e].t;
+    }
   }
   for (int I = 0; I < nc; ++I) Ac->rp[I + 1] += Ac->rp[I];
   free(T);
@@ -338,16 +355,16 @@ static int galerkin(const or_csr *A, int nc, const int *agg, const double *p, or
 long or_galerkin_nnz(int n, const int *rp, const int *ci, const double *val, int nc,
                      const int *agg, const double *p) {
   or_csr A = {n, rp[n], (int *)rp, (int *)ci, (double *)val}, Ac = {0};
-  if (galerkin(&A, nc, agg, p, &Ac) != OR_OK) return -1;
+  if (galerkin(&A, nc, agg, p, 0, &Ac) != OR_OK) return -1;
   long z = Ac.nnz;
   csr_free(&Ac);
   return z;
 }
 
 int or_galerkin(int n, const int *rp, const int *ci, const double *val, int nc,
-                const int *agg, const double *p, int *rpc, int *cic, double *valc) {
+                const int *agg, const double *p, int f32, int *rpc, int *cic, double *valc) {
   or_csr A = {n, rp[n], (int *)rp, (int *)ci, (double *)val}, Ac = {0};
-  int st = galerkin(&A, nc, agg, p, &Ac);
+  int st = galerkin(&A, nc, agg, p, f32, &Ac);
   if (st != OR_OK) return st;
   memcpy(rpc, Ac.rp, sizeof(int) * ((size_t)nc + 1));
   memcpy(cic, Ac.ci, sizeof(int) * (size_t)Ac.nnz);
@@ -403,9 +420,12 @@ void or_free(or_hier *h) {
 
 /* Build the hierarchy: levels while n_k > coarse_max and nl < max_levels; each level
  * does `sweeps` pairwise matching sweeps; stops early when a sweep forms no pair, and,
- * when stall_ratio > 0, after a level whose coarsening ratio n_k / n_{k+1} is below it. */
+ * when stall_ratio > 0, after a level whose coarsening ratio n_k / n_{k+1} is below it.
+ * galerkin_fp32_from = k >= 1 forms the operators of levels k, k+1, ... (and the
+ * intermediate operators of their sweeps) with the binary32 Galerkin product; 0: none. */
 or_hier *or_setup(int n, const int *rp, const int *ci, const double *val, const double *v,
-                  int sweeps, int coarse_max, int max_levels, double stall_ratio, int *status) {
+                  int sweeps, int coarse_max, int max_levels, double stall_ratio,
+                  int galerkin_fp32_from, int *status) {
   *status = OR_OK;
   if (n <= 0 || sweeps < 1 || sweeps > OR_MAX_SWEEPS || max_levels < 1 ||
       max_levels > OR_MAX_LEVELS || or_check_csr(n, rp, ci) != OR_OK) {
@@ -461,7 +481,7 @@ or_hier *or_setup(int n, const int *rp, const int *ci, const double *val, const 
       double *vc = (double *)xcalloc((size_t)nc, sizeof(double));
       or_prolongator(ns, nc, agg, vcur, p, vc);
       or_csr next = {0};
-      st = galerkin(&cur, nc, agg, p, &next);
+      st = galerkin(&cur, nc, agg, p, galerkin_fp32_from > 0 && h->nl >= galerkin_fp32_from, &next);
       if (st != OR_OK) { *status = st; free(agg); free(p); free(vc); break; }
       /* compose: row i of P_1...P_s has column agg_s[agg_tot[i]] and value
        * p_tot[i] * p_s[agg_tot[i]] */

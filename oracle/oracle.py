@@ -58,8 +58,8 @@ def _load():
             "or_aggregate": (i, [i, _i32p, _i32p, C.POINTER(i), C.POINTER(i)]),
             "or_prolongator": (i, [i, i, _i32p, _f64p, _f64p, _f64p]),
             "or_galerkin_nnz": (l, [i, _i32p, _i32p, _f64p, i, _i32p, _f64p]),
-            "or_galerkin": (i, [i, _i32p, _i32p, _f64p, i, _i32p, _f64p, _i32p, _i32p, _f64p]),
-            "or_setup": (vp, [i, _i32p, _i32p, _f64p, _f64p, i, i, i, d, C.POINTER(i)]),
+            "or_galerkin": (i, [i, _i32p, _i32p, _f64p, i, _i32p, _f64p, i, _i32p, _i32p, _f64p]),
+            "or_setup": (vp, [i, _i32p, _i32p, _f64p, _f64p, i, i, i, d, i, C.POINTER(i)]),
             "or_set_cycle": (None, [vp, i, i, i]),
             "or_set_gamma": (None, [vp, i]),
             "or_num_levels": (i, [vp]),
@@ -150,8 +150,9 @@ def prolongator(agg, nc, v):
     return p, vc
 
 
-def galerkin(rp, ci, val, agg, nc, p):
-    """A_c = P^T A P as a CSR triple, in the canonical summation order."""
+def galerkin(rp, ci, val, agg, nc, p, fp32=False):
+    """A_c = P^T A P as a CSR triple, in the canonical summation order (fp32: terms and
+    sums in binary32, stored as doubles)."""
     rp, ci, val = _csr(rp, ci, val)
     agg = np.ascontiguousarray(agg, dtype=np.int32)
     p = np.ascontiguousarray(p, dtype=np.float64)
@@ -163,7 +164,7 @@ def galerkin(rp, ci, val, agg, nc, p):
     rpc = np.empty(nc + 1, np.int32)
     cic = np.empty(z, np.int32)
     valc = np.empty(z, np.float64)
-    if lib.or_galerkin(n, rp, ci, val, nc, agg, p, rpc, cic, valc) != OK:
+    if lib.or_galerkin(n, rp, ci, val, nc, agg, p, 1 if fp32 else 0, rpc, cic, valc) != OK:
         raise MemoryError
     return rpc, cic, valc
 
@@ -172,13 +173,13 @@ class Hierarchy:
     """An oracle hierarchy (levels of A^k, composed P^k, smooth vectors)."""
 
     def __init__(self, rp, ci, val, v, sweeps=2, coarse_max=40, max_levels=40,
-                 pre=1, post=1, coarse_sweeps=20, stall_ratio=0.0, gamma=1):
+                 pre=1, post=1, coarse_sweeps=20, stall_ratio=0.0, gamma=1, galerkin_fp32_from=0):
         rp, ci, val = _csr(rp, ci, val)
         v = np.ascontiguousarray(v, dtype=np.float64)
         self._lib = _load()
         st = C.c_int(0)
         self._h = self._lib.or_setup(len(rp) - 1, rp, ci, val, v, sweeps, coarse_max,
-                                     max_levels, float(stall_ratio), C.byref(st))
+                                     max_levels, float(stall_ratio), int(galerkin_fp32_from), C.byref(st))
         if not self._h:
             raise ValueError(f"oracle setup failed with status {st.value}")
         self._lib.or_set_cycle(self._h, pre, post, coarse_sweeps)

@@ -230,3 +230,98 @@ def test_hierarchy_stall_ratio_stops_hub_growth():
     ns2 = [H2.level_n(k) for k in range(H2.nl)]
     k = next(i for i in range(1, len(ns)) if ns[i - 1] < 1.2 * ns[i])
     assert ns2 == ns[:k + 1]
+
+
+# ------------------------------------------------ binary32 Galerkin variant ----
+
+def test_galerkin_fp32_accumulates_in_binary32():
+    """Hand-worked case: one aggregate {0, 1}, p = 1, a_00 = 1, a_01 = a_10 = 2^-24,
+    a_11 = 1/2.  The four terms in canonical order are 1, 2^-24, 2^-24, 1/2.  In binary32
+    1 + 2^-24 rounds (to even) back to 1 twice, so the entry is exactly 1.5; a double sum
+    rounded once at the end would give 1.5 + 2^-23 instead."""
+    rp = np.array([0, 2, 4], np.int32)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    val = np.array([1.0, 2.0 ** -24, 2.0 ** -24, 0.5])
+    agg = np.zeros(2, np.int32)
+    rpc, cic, valc = oracle.galerkin(rp, ci, val, agg, 1, np.ones(2), fp32=True)
+    assert valc[0] == 1.5
+    rpc, cic, valc = oracle.galerkin(rp, ci, val, agg, 1, np.ones(2))
+    assert valc[0] == 1.5 + 2.0 ** -23
+
+
+def test_galerkin_fp32_rounds_the_inputs():
+    """p = 1 + 2^-30 is 1 in binary32, so the binary32 entry of a singleton aggregate is
+    exactly float(a_00); the binary64 entry carries the factor (1 + 2^-30)^2."""
+    rp = np.array([0, 1], np.int32)
+    ci = np.array([0], np.int32)
+    val = np.array([3.0])
+    p = np.array([1.0 + 2.0 ** -30])
+    assert oracle.galerkin(rp, ci, val, np.zeros(1, np.int32), 1, p, fp32=True)[2][0] == 3.0
+    assert oracle.galerkin(rp, ci, val, np.zeros(1, np.int32), 1, p)[2][0] == (p[0] * p[0]) * 3.0
+
+
+@pytest.mark.parametrize("kind,seed", [("rand", 0), ("ties", 2), ("diff", 3)])
+def test_galerkin_fp32_error_bound(kind, seed):
+    """Each binary32 entry is within 9u (u = 2^-24) of the exact P^T A P entry, relative to
+    (|P|^T |A| |P|)_IJ: three input roundings and two products per term, at most three
+    additions over at most four terms.  Entries are binary32 numbers, the pattern is the
+    binary64 product's, and A_c is bit-symmetric."""
+    if kind == "diff":
+        rp, ci, val = P.lognormal_diffusion(10, seed=seed)
+        n = len(rp) - 1
+        v = np.ones(n)
+    else:
+        n = 1500
+        rp, ci, val = P.random_spd(n, 6.0, seed=seed, ties=kind == "ties")
+        v = np.random.default_rng(seed).uniform(0.5, 2, n)
+    mate, agg, nc, _, _, p, vc = _one_sweep(rp, ci, val, v)
+    r32, c32, v32 = oracle.galerkin(rp, ci, val, agg, nc, p, fp32=True)
+    r64, c64, v64 = oracle.galerkin(rp, ci, val, agg, nc, p)
+    assert np.array_equal(r32, r64) and np.array_equal(c32, c64)
+    assert np.array_equal(v32, v32.astype(np.float32).astype(np.float64))
+    assert oracle.check_symmetric(r32, c32, v32)
+    A = P.to_scipy(rp, ci, val)
+    Pm = _P_matrix(agg, p, nc)
+    exact = (Pm.T @ A @ Pm).toarray()
+    mag = (abs(Pm).T @ abs(A) @ abs(Pm)).toarray()
+    got = sp.csr_matrix((v32, c32, r32), shape=(nc, nc)).toarray()
+    assert np.all(np.abs(got - exact) <= 9 * 2.0 ** -24 * mag + 1e-300)
+    # and it is not the binary64 product: some entry differs
+    assert np.any(v32 != v64)
+
+
+def test_hierarchy_fp32_galerkin_poisson_closed_form():
+    """3D Poisson, v = 1: equal entries see equal binary32 roundings, so ties stay ties and
+    the hierarchy keeps the closed-form structure (2x2x2 cubes, A^k = 2^-k L_7 on
+    (16/2^k)^3); the values carry only the binary32 rounding of the p's (1/sqrt 2 is not a
+    binary32 number) and of three products per level: within 3 * 9u per level relative."""
+    rp, ci, val = P.poisson3d(16)
+    n = len(rp) - 1
+    H64 = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=3, coarse_max=10)
+    H32 = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=3, coarse_max=10, galerkin_fp32_from=1)
+    assert H32.nl == H64.nl == 4
+    for k in range(H64.nl):
+        a, b = H64.level(k), H32.level(k)
+        assert np.array_equal(a["rp"], b["rp"]) and np.array_equal(a["ci"], b["ci"])
+        if k < H64.nl - 1:
+            assert np.array_equal(a["agg"], b["agg"])
+        m = 16 >> k
+        rows = np.repeat(np.arange(m ** 3), np.diff(b["rp"]))
+        ref = np.where(b["ci"] == rows, 6.0, -1.0) * 0.5 ** k
+        assert np.all(np.abs(b["val"] - ref) <= k * 27 * 2.0 ** -24 * np.abs(ref))
+        if k >= 1:
+            assert np.any(b["val"] != ref)
+
+
+def test_hierarchy_fp32_galerkin_from_level():
+    """galerkin_fp32_from = 2 keeps levels 0 and 1 binary64 (bit-equal to the plain
+    hierarchy) and forms the later levels in binary32."""
+    rp, ci, val = P.lognormal_diffusion(12, seed=5)
+    n = len(rp) - 1
+    H64 = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=2, coarse_max=20)
+    H2 = oracle.Hierarchy(rp, ci, val, np.ones(n), sweeps=2, coarse_max=20, galerkin_fp32_from=2)
+    assert H64.nl >= 4
+    for k in (0, 1):
+        assert np.array_equal(H64.level(k)["val"], H2.level(k)["val"])
+    L2 = H2.level(2)["val"]
+    assert np.array_equal(L2, L2.astype(np.float32).astype(np.float64))
