@@ -292,23 +292,27 @@ def run_cuda(args, rank, world, dist):
                     "traffic": _traffic_for(dominant), "launches": nl,
                     "bytes_per_launch": byt / nl, "avg_launch_us": ms / nl * 1e3}
 
-    # FP32 V-cycle variant on the same workload (not part of the timed value)
-    variant = None
+    # precision variants on the same workload (not part of the timed value): the other
+    # V-cycle precision, and binary32 Galerkin products for every coarse operator with the
+    # float32 V-cycle
+    variants = []
     if args.variant and dist is None:
-        prm32 = B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, vcycle_fp32=int(not fp32),
-                                     check_input=0, **extra)
-        res = []
-        for _ in range(3):
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            h, st, info = step(prm32, e)
-            h.free()
-            torch.cuda.synchronize()
-            res.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), info))
-        best = min(res, key=lambda r: r[0] + r[1])
-        variant = {"vcycle": "fp32" if not fp32 else "fp64", "ms_per_step": round(best[0] + best[1], 3),
-                   "setup_ms": round(best[0], 3), "solve_ms": round(best[1], 3), "iters": best[2]["iters"],
-                   "rel_res_true": best[2]["rel_res_true"],
-                   "err_vs_xstar": float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))}
+        for vf32, gf32 in ((int(not fp32), 0), (1, 1)):
+            prmv = B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, vcycle_fp32=vf32,
+                                        galerkin_fp32_from=gf32, check_input=0, **extra)
+            res = []
+            for _ in range(3):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                h, st, info = step(prmv, e)
+                h.free()
+                torch.cuda.synchronize()
+                res.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), info,
+                            float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))))
+            best = min(res, key=lambda r: r[0] + r[1])
+            variants.append({"vcycle": "fp32" if vf32 else "fp64", "galerkin": "fp32" if gf32 else "fp64",
+                             "ms_per_step": round(best[0] + best[1], 3), "setup_ms": round(best[0], 3),
+                             "solve_ms": round(best[1], 3), "iters": best[2]["iters"],
+                             "rel_res_true": best[2]["rel_res_true"], "err_vs_xstar": best[3]})
 
     # CPU baseline: the oracle as it stands, one full step, rank 0 at N=1 only
     cpu = None
@@ -336,8 +340,8 @@ def run_cuda(args, rank, world, dist):
         "kernel_classes": sorted([{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
                                   for e in trace_all], key=lambda e: -e["total_ms"])[:12],
     }
-    if variant:
-        out["variant"] = variant
+    if variants:
+        out["variants"] = variants
     if rank == 0:
         print(json.dumps(out))
 
@@ -401,7 +405,8 @@ def main():
     ap.add_argument("--fp32", type=int, default=None, help="override the workload's V-cycle precision")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--itmax", type=int, default=5000)
-    ap.add_argument("--variant", type=int, default=1, help="also time the other V-cycle precision")
+    ap.add_argument("--variant", type=int, default=1,
+                    help="also time the precision variants (other V-cycle precision; binary32 Galerkin)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no e2e, variant, CPU baseline): for ncu launch lists")

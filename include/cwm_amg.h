@@ -72,6 +72,12 @@ typedef struct {
                            0 = off (default) */
   int gamma;            /* coarse cycles per level: 1 = V-cycle (default), 2 = W-cycle
                            (Sec. 5.1; its cost grows as 2^levels) */
+  int galerkin_fp32_from; /* k >= 1: the operators of levels k, k+1, ... (and the
+                           intermediate operators of their sweeps) come from a binary32
+                           Galerkin product: p_i, p_j, a_ij rounded to float, terms and
+                           sums in float in the canonical order, stored as doubles (the
+                           precision trade-off of Sec. 3.2 carried over to the setup; the
+                           finest operator stays the caller's); 0 = off (default) */
 } amg_params;
 
 /* Statistics filled by amg_pcg_solve and amg_stats. */
@@ -196,12 +202,14 @@ amg_status cwm_aggregate(int n, const int32_t *d_mate, const double *d_v, int32_
  * (min(i,j), max(i,j), i) order; every hit (I,J) is stored, columns ascending.
  *   d_rpc (nc+1), d_colc and d_valc (capacity entries each) are device outputs;
  *   capacity >= nnz always suffices.  h_nnzc receives nnz(A_c).
+ *   fp32 = 1: the binary32 variant (p_i, p_j, a_ij rounded to float, terms and sums in
+ *   float in the same order, each entry stored as the double of its float); 0: float64.
  * Errors: INVALID_ARG (an aggregate with more than two members), UNSUPPORTED (a coarse
  * row gathering more than 8192 fine entries), OOM.  Synchronises. */
 amg_status cwm_galerkin(int n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
                         int nc, const int32_t *d_agg, const double *d_p, int32_t *d_rpc,
                         int32_t *d_colc, double *d_valc, int64_t capacity, int64_t *h_nnzc,
-                        void *stream);
+                        int fp32, void *stream);
 
 /* ---- Differentiation of a solve x = A^{-1} b ---- */
 

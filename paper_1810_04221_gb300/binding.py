@@ -46,6 +46,7 @@ class AmgParams(C.Structure):
         ("tail_rows", C.c_int),
         ("stall_ratio", C.c_double),
         ("gamma", C.c_int),
+        ("galerkin_fp32_from", C.c_int),
     ]
 
 
@@ -107,7 +108,7 @@ def load(path: str | None = None):
             "cwm_suitor_match_noalloc": (i, [i, i64, vp, vp, vp, vp, vp]),
             "cwm_pattern_outer": (i, [i, i64, vp, vp, vp, vp, d, vp, vp]),
             "cwm_aggregate": (i, [i, vp, vp, vp, vp, vp, ip, ip, vp]),
-            "cwm_galerkin": (i, [i, vp, vp, vp, i, vp, vp, vp, vp, vp, i64, C.POINTER(i64), vp]),
+            "cwm_galerkin": (i, [i, vp, vp, vp, i, vp, vp, vp, vp, vp, i64, C.POINTER(i64), i, vp]),
             "amg_trace_enable": (i, [vp, i, C.c_char_p]),
             "amg_trace_reset": (i, [vp]),
             "amg_trace_count": (i, [vp]),
@@ -300,8 +301,9 @@ def cwm_aggregate(mate, v, stream=None):
     return agg, p, vc[: nc.value], nc.value, npairs.value
 
 
-def cwm_galerkin(row_ptr, col, val, nc: int, agg, p, stream=None):
-    """Returns (rpc, colc, valc) of A_c = P^T A P for a pairwise P."""
+def cwm_galerkin(row_ptr, col, val, nc: int, agg, p, fp32: bool = False, stream=None):
+    """Returns (rpc, colc, valc) of A_c = P^T A P for a pairwise P (fp32: the binary32
+    product, values stored as doubles)."""
     n, nnz = row_ptr.numel() - 1, col.numel()
     dev = val.device
     rpc = torch.empty(nc + 1, dtype=torch.int32, device=dev)
@@ -313,7 +315,7 @@ def cwm_galerkin(row_ptr, col, val, nc: int, agg, p, stream=None):
                                _dev(val, torch.float64, "val", nnz), nc, _dev(agg, torch.int32, "agg", n),
                                _dev(p, torch.float64, "p", n), _dev(rpc, torch.int32, "rpc"),
                                _dev(colc, torch.int32, "colc"), _dev(valc, torch.float64, "valc"), cap,
-                               C.byref(nnzc), _stream(stream)), "cwm_galerkin")
+                               C.byref(nnzc), 1 if fp32 else 0, _stream(stream)), "cwm_galerkin")
     z = nnzc.value
     return rpc, colc[:z], valc[:z]
 

@@ -43,11 +43,13 @@ struct Level {
   CsrView<double> view64() const {
     CsrView<double> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val.get(); a.tile = tile;
+    a.rb = row_blocks_for(n, nnz);
     return a;
   }
   CsrView<float> view32() const {
     CsrView<float> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get(); a.tile = tile;
+    a.rb = row_blocks_for(n, nnz);
     return a;
   }
 };
@@ -178,6 +180,10 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   cudaStream_t s = h->stream;
   Level &F = h->lev.back();
   const int S = h->prm.sweeps_per_level;
+  // the level being built is lev.size(); its operators use the binary32 product from
+  // level galerkin_fp32_from on
+  const bool fp32_galerkin =
+      h->prm.galerkin_fp32_from > 0 && (int)h->lev.size() >= h->prm.galerkin_fp32_from;
   *made = false;
   LevelTag tag((int)h->lev.size() - 1);
 
@@ -246,7 +252,7 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
     CWM_TRY(galerkin_count(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(), gw,
                            h->err.get(), s));
     CWM_TRY(galerkin_fill(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(),
-                          o.ci.get(), o.val.get(), o.diag.get(), nullptr, gw, h->err.get(), s));
+                          o.ci.get(), o.val.get(), o.diag.get(), nullptr, gw, fp32_galerkin, h->err.get(), s));
     CWM_CUDA(cudaMemcpyAsync(h->box.ints + 4, o.rp.get() + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
     CWM_TRY(read_err(h, "amg_setup (Galerkin)"));
     o.nnz = h->box.ints[4];
@@ -459,8 +465,9 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   // The default cycle from zero (one pre- and one post-sweep) on a small level: the first
   // sweep x = D^{-1} b is formed on the fly inside the residual and the coarse correction
   // inside the post-sweep, two kernels fewer.  On large levels the extra gathers per
-  // nonzero cost more than the passes they save (measured), so they keep separate kernels.
-  if (zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= kFuseMaxRows) {
+  // nonzero cost more than the passes they save (measured), so they keep separate kernels;
+  // so do levels on sub-warp tiles (the fused forms exist as row-block kernels only).
+  if (zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= kFuseMaxRows && A.rb) {
     CWM_TRY(resid_scaled_restrict<V>(A, C0.n, L.mptr.get(), L.mlist.get(), LV::p(L), dinv, b, t1, LV::b(C0), s));
     for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C0), LV::x(C0), g == 0));
     return prolong_jacobi<V>(A, dinv, b, L.agg.get(), LV::p(L), LV::x(C0), x, s);
@@ -531,6 +538,7 @@ void amg_default_params(amg_params *p) {
   p->tail_rows = -1;
   p->stall_ratio = 0.0;
   p->gamma = 1;
+  p->galerkin_fp32_from = 0;
 }
 
 const char *amg_status_string(amg_status s) {
@@ -563,7 +571,7 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   h->trace.filter = P.trace_filter;
   TraceGuard tg(h);
   if (P.sweeps_per_level < 1 || P.sweeps_per_level > kMaxSweeps || P.max_levels < 1 || P.pre_sweeps < 0 ||
-      P.post_sweeps < 0 || P.coarse_sweeps < 0 || P.coarse_max < 0) {
+      P.post_sweeps < 0 || P.coarse_sweeps < 0 || P.coarse_max < 0 || P.galerkin_fp32_from < 0) {
     set_error("amg_setup: parameter out of range");
     return AMG_ERR_INVALID_ARG;
   }
@@ -1049,7 +1057,7 @@ amg_status cwm_aggregate(int n, const int32_t *d_mate, const double *d_v, int32_
 
 amg_status cwm_galerkin(int n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val, int nc,
                         const int32_t *d_agg, const double *d_p, int32_t *d_rpc, int32_t *d_colc, double *d_valc,
-                        int64_t capacity, int64_t *h_nnzc, void *stream) {
+                        int64_t capacity, int64_t *h_nnzc, int fp32, void *stream) {
   if (n < 0 || nc < 0 || nc > n || (n > 0 && (!d_row_ptr || !d_agg || !d_p)) || !d_rpc || capacity < 0) {
     set_error("cwm_galerkin: invalid argument");
     return AMG_ERR_INVALID_ARG;
@@ -1086,7 +1094,7 @@ amg_status cwm_galerkin(int n, const int32_t *d_row_ptr, const int32_t *d_col, c
     return AMG_ERR_INVALID_ARG;
   }
   CWM_TRY(galerkin_fill(d_row_ptr, d_col, d_val, nc, m1.get(), m2.get(), d_agg, d_p, d_rpc, d_colc, d_valc, nullptr,
-                        nullptr, gw, err.get(), s));
+                        nullptr, gw, fp32 != 0, err.get(), s));
   return read_bits(err.get(), &h_err, s, "cwm_galerkin (fill)");
 }
 

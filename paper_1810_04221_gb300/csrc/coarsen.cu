@@ -250,6 +250,9 @@ amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, cons
 }
 
 // ------------------------------------------------------------ Suitor ----
+#ifndef CWM_SUITOR_ENTRIES_PER_LANE
+#define CWM_SUITOR_ENTRIES_PER_LANE 1
+#endif
 // Sec. 3.1.  S[x] = (weight bits, suitor + 1) packed in 16 bytes; weights are positive
 // doubles, whose bit patterns order like their values, so the 128-bit pair compares
 // lexicographically as (weight, suitor index).  A proposer u beats the current suitor s
@@ -282,9 +285,11 @@ __global__ void k_clear_keys(long long n, SKey *S) {
 }
 
 // One T-lane tile per vertex u (grid-stride).  The tile finds the best neighbour that
-// would accept the current proposer, lane 0 installs the proposal with a 128-bit CAS,
-// and a displaced suitor becomes the next proposer (the chain is followed by the same
-// tile).  Every loop is capped; hitting a cap raises kErrTimeout and ends the tile.
+// would accept the current proposer; the lane that found it installs the proposal with a
+// 128-bit CAS, taking the key it has just read as the expected value (one dependent
+// memory round trip less per proposal), and a displaced suitor becomes the next proposer
+// (the chain is followed by the same tile).  Every loop is capped; hitting a cap raises
+// kErrTimeout and ends the tile.
 template <int T>
 __global__ void __launch_bounds__(256) k_suitor(int n, const int *__restrict__ rp,
                                                 const int *__restrict__ ci,
@@ -303,19 +308,23 @@ __global__ void __launch_bounds__(256) k_suitor(int n, const int *__restrict__ r
         break;
       }
       const unsigned long long me = (unsigned long long)current + 1ull;
-      unsigned long long bc = 0ull;
-      int bx = -1;
+      unsigned long long mc = 0ull;  // this lane's best candidate and the key it read there
+      int mx = -1;
+      SKey mk;
+      mk.lo = mk.hi = 0ull;
       const int s = rp[current], e = rp[current + 1];
       for (int k = s + lane; k < e; k += T) {
         const double c = w[k];
         if (!(c > 0.0)) continue;
         const int x = ci[k];
         const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
-        if (cb > bc || (cb == bc && x > bx)) {
+        if (cb > mc || (cb == mc && x > mx)) {
           const SKey cur = load_key(S + x);
-          if (gt(cb, me, cur.hi, cur.lo)) { bc = cb; bx = x; }
+          if (gt(cb, me, cur.hi, cur.lo)) { mc = cb; mx = x; mk = cur; }
         }
       }
+      unsigned long long bc = mc;
+      int bx = mx;
 #pragma unroll
       for (int o = T / 2; o > 0; o >>= 1) {
         const unsigned long long oc = tile.shfl_xor(bc, o);
@@ -323,12 +332,13 @@ __global__ void __launch_bounds__(256) k_suitor(int n, const int *__restrict__ r
         if (oc > bc || (oc == bc && ox > bx)) { bc = oc; bx = ox; }
       }
       if (bx < 0) break;  // nobody would accept `current`: it stays unmatched
+      const int src = __ffs(tile.ballot(mx == bx)) - 1;  // the lane holding bx (>= 1 lane)
       int next = -2;      // -2: beaten while proposing, rescan
-      if (lane == 0) {
+      if (lane == src) {
         SKey mine;
         mine.lo = me;
         mine.hi = bc;
-        SKey expect = load_key(S + bx);
+        SKey expect = mk;
         for (int t = 0; t < (1 << 22); ++t) {
           if (!gt(bc, me, expect.hi, expect.lo)) break;
           const SKey old = atomicCAS(S + bx, expect, mine);
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(256) k_suitor(int n, const int *__restrict__ r
           expect = old;
         }
       }
-      next = tile.shfl(next, 0);
+      next = tile.shfl(next, src);
       if (next == -2) continue;
       if (next < 0) break;
       current = next;
@@ -366,7 +376,9 @@ amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, cons
   CWM_LAUNCH();
   if (cap <= 0) cap = nnz + (long long)n + 1024;
   const double mean = n ? (double)nnz / n : 1.0;
-  const int T = tile_for_mean(mean);
+  // Proposals are latency-bound: a tile of half the row length (two entries per lane)
+  // keeps twice as many proposal chains in flight.
+  const int T = tile_for_mean(mean / CWM_SUITOR_ENTRIES_PER_LANE);
   const int block = 256;
   const int grid = grid_for((long long)n * T, block, num_sms() * 8);
   switch (T) {

@@ -47,10 +47,11 @@ amg_status galerkin_count(const int *rp, const int *ci, const double *val, int n
                           const int *m2, const int *agg, const double *p, int *rpc,
                           const GalerkinWork &work, int *d_err, cudaStream_t s);
 // Pass 2: columns and values of A_c at rpc; diag_c (nc) and dl1_c (nc) may be NULL.
+// fp32: terms and sums in binary32 (values stored as doubles of floats).
 amg_status galerkin_fill(const int *rp, const int *ci, const double *val, int nc, const int *m1,
                          const int *m2, const int *agg, const double *p, const int *rpc, int *cic,
                          double *valc, double *diag_c, double *dl1_c, const GalerkinWork &work,
-                         int *d_err, cudaStream_t s);
+                         bool fp32, int *d_err, cudaStream_t s);
 // m1/m2 from agg when the caller only has agg (cwm_galerkin): members in ascending order;
 // an empty aggregate or one with more than two members raises kErrInvalid.  cnt: nc ints.
 amg_status members_from_agg(int n, int nc, const int *agg, int *m1, int *m2, int *cnt, int *d_err,

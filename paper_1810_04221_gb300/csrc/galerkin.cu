@@ -7,7 +7,9 @@
 // run's value sums t_ij = (p_i p_j) a_ij from +0.0 in ascending (min(i,j), max(i,j), i)
 // order with round-to-nearest intrinsics, which makes the result independent of the
 // thread schedule and bit-symmetric.  Rows gathering more than kWarpCap entries go to a
-// block-per-row kernel (up to kBlockCap entries).
+// block-per-row kernel (up to kBlockCap entries).  The fill pass has a binary32 variant
+// (Acc = float): p_i, p_j and a_ij rounded to float, terms and sums in float in the same
+// order, each entry stored as the double of its float.
 #include <climits>
 
 #include "coarsen.cuh"
@@ -49,12 +51,36 @@ __device__ __forceinline__ unsigned long long make_key(const RowSrc &r, int q, c
   return ((unsigned long long)J << 32) | (unsigned)q;
 }
 
+// Round-to-nearest arithmetic of the accumulation type (no contraction into FMA).
+template <class Acc>
+struct Arith;
+template <>
+struct Arith<double> {
+  static __device__ __forceinline__ double in(double x) { return x; }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+};
+template <>
+struct Arith<float> {
+  static __device__ __forceinline__ float in(double x) { return __double2float_rn(x); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+};
+
+// t_ij = (p_i p_j) a_ij in the accumulation type
+template <class Acc>
+__device__ __forceinline__ Acc term(double pi, double pj, double a) {
+  using M = Arith<Acc>;
+  return M::mul(M::mul(M::in(pi), M::in(pj)), M::in(a));
+}
+
 // Sum of one run of equal J (length len <= 4) starting at sorted position q.
+template <class Acc>
 __device__ __forceinline__ double run_value(const RowSrc &r, const unsigned long long *keys, int q, int len,
                                             const int *__restrict__ ci, const double *__restrict__ val,
                                             const double *__restrict__ p) {
   int kmin[4], kmax[4], ii[4];
-  double t[4];
+  Acc t[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (e < len) {
@@ -63,12 +89,12 @@ __device__ __forceinline__ double run_value(const RowSrc &r, const unsigned long
       const int i = first ? r.i1 : r.i2;
       const int k = first ? r.s1 + local : r.s2 + (local - r.L1);
       const int j = ci[k];
-      t[e] = __dmul_rn(__dmul_rn(p[i], p[j]), val[k]);
+      t[e] = term<Acc>(p[i], p[j], val[k]);
       kmin[e] = i < j ? i : j;
       kmax[e] = i < j ? j : i;
       ii[e] = i;
     } else {
-      t[e] = 0.0;
+      t[e] = Acc(0);
       kmin[e] = kmax[e] = ii[e] = INT_MAX;
     }
   }
@@ -82,7 +108,7 @@ __device__ __forceinline__ double run_value(const RowSrc &r, const unsigned long
                                                     (kmax[b] == kmax[b - 1] && ii[b] < ii[b - 1])));
       if (swap) {
         int x;
-        double y;
+        Acc y;
         x = kmin[b]; kmin[b] = kmin[b - 1]; kmin[b - 1] = x;
         x = kmax[b]; kmax[b] = kmax[b - 1]; kmax[b - 1] = x;
         x = ii[b]; ii[b] = ii[b - 1]; ii[b - 1] = x;
@@ -90,11 +116,11 @@ __device__ __forceinline__ double run_value(const RowSrc &r, const unsigned long
       }
     }
   }
-  double sum = 0.0;
+  Acc sum = Acc(0);
 #pragma unroll
   for (int e = 0; e < 4; ++e)
-    if (e < len) sum = __dadd_rn(sum, t[e]);
-  return sum;
+    if (e < len) sum = Arith<Acc>::add(sum, t[e]);
+  return (double)sum;
 }
 
 __device__ __forceinline__ int next_pow2(int x) {
@@ -109,7 +135,7 @@ __device__ __forceinline__ int next_pow2(int x) {
 // sort is needed: the lowest lane of each equal-J group leads it, counts it, and in the
 // fill pass gathers the group's (at most four) terms with shuffles, orders them by
 // (min(i,j), max(i,j), i), sums them from +0.0, and writes at its rank among the leaders.
-template <bool FILL>
+template <bool FILL, class Acc>
 __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigned gmask, int gbase, int glen,
                                                  const int *__restrict__ ci, const double *__restrict__ val,
                                                  const int *__restrict__ agg, const double *__restrict__ p,
@@ -136,10 +162,10 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
     if (gl == 0) cnt[I] = __popc(lead);
     return;
   }
-  double t = 0.0;
+  Acc t = Acc(0);
   int kmin = 0, kmax = 0;
   if (act) {
-    t = __dmul_rn(__dmul_rn(p[i], p[j]), val[k]);
+    t = term<Acc>(p[i], p[j], val[k]);
     kmin = min(i, j);
     kmax = max(i, j);
   }
@@ -151,7 +177,7 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
     src[m] = rest ? __ffs(rest) - 1 : lane;
     rest &= rest - 1u;
   }
-  double tm[4];
+  Acc tm[4];
   int kmn[4], kmx[4], im[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -170,7 +196,7 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
   const int len = members < 4 ? members : 4;
 #pragma unroll
   for (int m = 0; m < 4; ++m)
-    if (m >= len) { kmn[m] = kmx[m] = im[m] = INT_MAX; tm[m] = 0.0; }
+    if (m >= len) { kmn[m] = kmx[m] = im[m] = INT_MAX; tm[m] = Acc(0); }
 #pragma unroll
   for (int a = 1; a < 4; ++a) {
 #pragma unroll
@@ -179,7 +205,7 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
                         (kmn[b] == kmn[b - 1] && (kmx[b] < kmx[b - 1] || (kmx[b] == kmx[b - 1] && im[b] < im[b - 1])));
       if (swap) {
         int x;
-        double y;
+        Acc y;
         x = kmn[b]; kmn[b] = kmn[b - 1]; kmn[b - 1] = x;
         x = kmx[b]; kmx[b] = kmx[b - 1]; kmx[b - 1] = x;
         x = im[b]; im[b] = im[b - 1]; im[b - 1] = x;
@@ -187,10 +213,11 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
       }
     }
   }
-  double sum = 0.0;
+  Acc acc = Acc(0);
 #pragma unroll
   for (int m = 0; m < 4; ++m)
-    if (m < len) sum = __dadd_rn(sum, tm[m]);
+    if (m < len) acc = Arith<Acc>::add(acc, tm[m]);
+  const double sum = (double)acc;
   const int out = rpc[I] + rank;
   cic[out] = (int)J;
   valc[out] = sum;
@@ -200,7 +227,7 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
 // ------------------------------------------------------------ shared-memory rows ----
 // A coarse row with 32 < L <= kWarpCap entries: keys (J, slot) sorted in shared memory by
 // the warp (bitonic), runs of equal J summed in canonical order.
-template <bool FILL>
+template <bool FILL, class Acc>
 __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsigned long long *keys,
                                                   const int *__restrict__ ci, const double *__restrict__ val,
                                                   const int *__restrict__ agg, const double *__restrict__ p,
@@ -238,7 +265,7 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
       int len = 1;
       while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
       if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
-      const double s = run_value(r, keys, q, len, ci, val, p);
+      const double s = run_value<Acc>(r, keys, q, len, ci, val, p);
       const int out = rpc[I] + base + __popc(ball & ((1u << lane) - 1u));
       cic[out] = (int)J;
       valc[out] = s;
@@ -255,7 +282,7 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
 // warp handles one in registers; otherwise the warp handles them in turn (registers up to
 // 32 entries, shared memory up to kWarpCap, longer rows queued for the block kernel).
 // FILL = false: cnt[I] = number of distinct J.  FILL = true: columns and values at rpc[I].
-template <bool FILL>
+template <bool FILL, class Acc>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_galerkin_warp(int nc, const int *__restrict__ rp, const int *__restrict__ ci,
                     const double *__restrict__ val, const int *__restrict__ m1,
@@ -280,7 +307,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int L0 = __shfl_sync(0xffffffffu, Lh, 0), L1 = __shfl_sync(0xffffffffu, Lh, 16);
     if (L0 <= 16 && L1 <= 16) {
       if (Ih < nc)
-        galerkin_row_reg<FILL>(rh, Ih, half ? 0xffff0000u : 0x0000ffffu, half * 16, 16, ci, val, agg, p, cnt, rpc,
+        galerkin_row_reg<FILL, Acc>(rh, Ih, half ? 0xffff0000u : 0x0000ffffu, half * 16, 16, ci, val, agg, p, cnt, rpc,
                                cic, valc, diag_c, err);
       __syncwarp();
       continue;
@@ -291,9 +318,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const RowSrc r = row_src(I, m1, m2, rp);
       const int L = r.L1 + r.L2;
       if (L <= 32) {
-        galerkin_row_reg<FILL>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+        galerkin_row_reg<FILL, Acc>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (L <= kWarpCap) {
-        galerkin_row_smem<FILL>(r, I, keys, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+        galerkin_row_smem<FILL, Acc>(r, I, keys, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (!FILL && lane == 0) {
         long_rows[atomicAdd(n_long, 1)] = I;
       }
@@ -303,7 +330,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 // ------------------------------------------------------------ long rows ----
-template <bool FILL>
+template <bool FILL, class Acc>
 __global__ void __launch_bounds__(kLongThreads)
     k_galerkin_block(const int *__restrict__ rp, const int *__restrict__ ci,
                      const double *__restrict__ val, const int *__restrict__ m1,
@@ -365,7 +392,7 @@ __global__ void __launch_bounds__(kLongThreads)
         int len = 1;
         while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
         if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
-        const double s = run_value(r, keys, q, len, ci, val, p);
+        const double s = run_value<Acc>(r, keys, q, len, ci, val, p);
         const int out = rpc[I] + base + before + __popc(ball & ((1u << lane) - 1u));
         cic[out] = (int)J;
         valc[out] = s;
@@ -398,9 +425,11 @@ static amg_status galerkin_attrs() {
   CWM_CUDA(cudaGetDevice(&dev));
   bool &attr = attr_set[dev & 63];
   if (!attr) {
-    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kBlockCap * 8));
-    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kBlockCap * 8));
+    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kBlockCap * 8));
     attr = true;
   }
@@ -420,10 +449,10 @@ amg_status galerkin_count(const int *rp, const int *ci, const double *val, int n
   const int block = kWarpsPerBlock * 32;
   const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
   CWM_CUDA(cudaMemsetAsync(work.n_long, 0, sizeof(int), s));
-  k_galerkin_warp<false><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, nullptr,
+  k_galerkin_warp<false, double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, nullptr,
                                                 nullptr, nullptr, nullptr, work.long_rows, work.n_long, d_err);
   CWM_LAUNCH();
-  k_galerkin_block<false><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+  k_galerkin_block<false, double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
       rp, ci, val, m1, m2, agg, p, work.cnt, nullptr, nullptr, nullptr, nullptr, nullptr,
       work.long_rows, work.n_long, d_err);
   CWM_LAUNCH();
@@ -433,19 +462,28 @@ amg_status galerkin_count(const int *rp, const int *ci, const double *val, int n
 amg_status galerkin_fill(const int *rp, const int *ci, const double *val, int nc, const int *m1,
                          const int *m2, const int *agg, const double *p, const int *rpc, int *cic,
                          double *valc, double *diag_c, double *dl1_c, const GalerkinWork &work,
-                         int *d_err, cudaStream_t s) {
+                         bool fp32, int *d_err, cudaStream_t s) {
   if (nc == 0) return AMG_OK;
   CWM_TRY(galerkin_attrs());
   // reads as in the count pass plus val and p; writes of A_c not included (size unknown here)
   CWM_TRACE("galerkin_fill", 12.0 * work.nnz_fine + 12.0 * work.n_fine + 44.0 * nc, s);
   const int block = kWarpsPerBlock * 32;
   const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
-  k_galerkin_warp<true><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic,
-                                               valc, diag_c, nullptr, nullptr, d_err);
-  CWM_LAUNCH();
-  k_galerkin_block<true><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
-      rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic, valc, diag_c, dl1_c, work.long_rows,
-      work.n_long, d_err);
+  if (fp32) {
+    k_galerkin_warp<true, float><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic,
+                                                        valc, diag_c, nullptr, nullptr, d_err);
+    CWM_LAUNCH();
+    k_galerkin_block<true, float><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+        rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic, valc, diag_c, dl1_c, work.long_rows,
+        work.n_long, d_err);
+  } else {
+    k_galerkin_warp<true, double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic,
+                                                         valc, diag_c, nullptr, nullptr, d_err);
+    CWM_LAUNCH();
+    k_galerkin_block<true, double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+        rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic, valc, diag_c, dl1_c, work.long_rows,
+        work.n_long, d_err);
+  }
   CWM_LAUNCH();
   return AMG_OK;
 }

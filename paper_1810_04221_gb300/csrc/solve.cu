@@ -191,6 +191,17 @@ __device__ __forceinline__ V rb_row_dot(const int *__restrict__ ci, const V *__r
 
 static int rb_grid(long long n) { return (int)((n + kRB - 1) / kRB); }
 
+#ifndef CWM_RB_MAX_MEAN
+#define CWM_RB_MAX_MEAN 16
+#endif
+#ifndef CWM_RB_MIN_BLOCKS_PER_SM
+#define CWM_RB_MIN_BLOCKS_PER_SM 8
+#endif
+bool row_blocks_for(int n, long long nnz) {
+  if (n <= 0) return true;
+  return (double)nnz / n <= CWM_RB_MAX_MEAN || rb_grid(n) >= (long long)num_sms() * CWM_RB_MIN_BLOCKS_PER_SM;
+}
+
 // Block sums of up to three values per thread with few FP64 instructions (blockDim ==
 // kRB): the values go to shared memory, then warp w folds value w (kRB/32 sequential adds
 // per lane and five shuffle steps).  GB300 retires FP64 adds as whole-warp instructions at
@@ -283,7 +294,12 @@ template <class V>
 amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V *y, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("jacobi", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 4.0 * sizeof(V) * A.n, s);
-  k_jacobi_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, y);
+  if (A.rb) {
+    k_jacobi_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, y);
+  } else {
+    CWM_DISPATCH_T(A.tile, (k_jacobi<V, kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b,
+                                                                                x, y)));
+  }
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -414,11 +430,34 @@ __global__ void __launch_bounds__(kRB) k_resid_rb(int n, const int *__restrict__
   if (threadIdx.x < nrows) r[i] = b[i] - dot;
 }
 
+// r = b - A x (x may be NULL: r = b), a sub-warp tile per row
+template <class V, int T>
+__global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                     const V *__restrict__ val, const V *__restrict__ b,
+                                                     const V *__restrict__ x, V *__restrict__ r) {
+  CWM_TILE_LOOP(T, n) {
+    const long long row = base + sub;
+    const bool active = row < n;
+    const V dot = tile_row_dot<V, T>(rp, ci, val, x, row, active, lane);
+    if (active && lane == 0) r[row] = b[row] - dot;
+  }
+}
+
+template <class V>
+static void launch_residual(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s) {
+  if (A.rb) {
+    k_resid_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r);
+  } else {
+    CWM_DISPATCH_T(A.tile, (k_residual<V, kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x,
+                                                                                  r)));
+  }
+}
+
 template <class V>
 amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
-  k_resid_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r);
+  launch_residual<V>(A, b, x, r, s);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -459,7 +498,7 @@ amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const
   if (nc == 0) return AMG_OK;
   {
     CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
-    k_resid_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r_scratch);
+    launch_residual<V>(A, b, x, r_scratch, s);
     CWM_LAUNCH();
   }
   CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
@@ -643,22 +682,11 @@ amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t 
 }
 
 // ------------------------------------------------------------ residual ----
-template <int T>
-__global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                     const double *__restrict__ val, const double *__restrict__ b,
-                                                     const double *__restrict__ x, double *__restrict__ r) {
-  CWM_TILE_LOOP(T, n) {
-    const long long row = base + sub;
-    const bool active = row < n;
-    const double dot = tile_row_dot<double, T>(rp, ci, val, x, row, active, lane);
-    if (active && lane == 0) r[row] = b[row] - dot;
-  }
-}
 
 amg_status residual(const CsrView<double> &A, const double *b, const double *x, double *r, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("residual", 4.0 * (A.n + 1) + 12.0 * A.nnz + 24.0 * A.n, s);
-  k_resid_rb<double><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r);
+  launch_residual<double>(A, b, x, r, s);
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -691,7 +719,11 @@ __global__ void __launch_bounds__(kRB) k_l1_rb(int n, const int *__restrict__ rp
 amg_status l1_norms(const CsrView<double> &A, double *d, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("l1_norms", 4.0 * (A.n + 1) + 8.0 * A.nnz + 8.0 * A.n, s);
-  k_l1_rb<<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.val, d);
+  if (A.rb) {
+    k_l1_rb<<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.val, d);
+  } else {
+    CWM_DISPATCH_T(A.tile, (k_l1<kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.val, d)));
+  }
   CWM_LAUNCH();
   return AMG_OK;
 }

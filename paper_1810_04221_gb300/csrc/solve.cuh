@@ -15,7 +15,14 @@ struct CsrView {
   const int *ci = nullptr;
   const V *val = nullptr;
   int tile = 8;  // sub-warp width chosen from the mean row length
+  bool rb = true;  // row-block kernels (else a sub-warp tile per row): row_blocks_for()
 };
+
+// Row-block kernels (a thread per row, CSR chunks staged in shared memory) suit short rows,
+// or levels with enough row blocks to fill the GPU; a level with long rows and few row
+// blocks (coarse vector-PDE operators) leaves most threads of a row block idle and takes
+// a sub-warp tile per row instead.
+bool row_blocks_for(int n, long long nnz);
 
 // Largest coarsest level solved by the one-block kernel (x kept in shared memory).
 constexpr int kCoarseBlockMax = 2048;

@@ -34,6 +34,8 @@ CASES = [
     ("poisson3d_24_s3", lambda: P.poisson3d(24), 3, 20),
     ("lognormal_16_s3", lambda: P.lognormal_diffusion(16, seed=3), 3, 30),
     ("rand_s2", lambda: P.random_spd(6000, 7.0, seed=21), 2, 40),
+    # long rows on small levels: every level on sub-warp tiles instead of row blocks
+    ("elasticity_8_s2", lambda: P.elasticity_q1(8), 2, 50),
 ]
 
 

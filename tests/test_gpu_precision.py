@@ -1,0 +1,182 @@
+"""GPU: the binary32 Galerkin product (coarse operators formed in float, the precision
+trade-off of Sec. 3.2 carried over to the setup) against the oracle's binary32 product.
+
+Bars: bit-exact against the oracle run with the same option (both sides round p_i, p_j and
+a_ij to float and form and sum the terms in float in the canonical order); against the
+float64 oracle, the coarse operators differ by float rounding only (relative 1e-5 where the
+patterns coincide) and FCG needs at most two more iterations.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1810_04221_gb300 import problems as P
+from tests.gpu_util import bits_equal, csr_dev, dev, host
+
+pytestmark = pytest.mark.gpu
+B = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global B
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_04221_gb300 import binding, build
+    build.build()
+    binding.load()
+    B = binding
+    yield
+
+
+def _cases():
+    out = [("poisson3d_12", P.poisson3d(12), None), ("lognormal_14", P.lognormal_diffusion(14, seed=7), None)]
+    rng = np.random.default_rng(0)
+    for seed, deg, ties in [(1, 3.0, False), (2, 7.0, True), (4, 40.0, False)]:
+        mat = P.random_spd(3001, deg, seed=seed, ties=ties)
+        out.append((f"rand_d{int(deg)}_s{seed}", mat, None if ties else rng.uniform(-1.5, 1.5, 3001)))
+    mat = P.elasticity_q1(6)
+    out.append(("elasticity_6", mat, P.smooth_vector_components(len(mat[0]) - 1, seed=1)))
+    return out
+
+
+CASES = _cases()
+IDS = [c[0] for c in CASES]
+
+
+def _v(mat, v):
+    return np.ones(len(mat[0]) - 1) if v is None else v
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_galerkin_fp32_bit_exact(case):
+    name, mat, v = case
+    v = _v(mat, v)
+    w = oracle.edge_weights(*mat, v)
+    mate = oracle.greedy_match(mat[0], mat[1], w)
+    agg, nc, _, _ = oracle.aggregate(mate)
+    p, _ = oracle.prolongator(agg, nc, v)
+    rpc_r, cic_r, valc_r = oracle.galerkin(*mat, agg, nc, p, fp32=True)
+    rpc, cic, valc = B.cwm_galerkin(*csr_dev(*mat), nc, dev(agg), dev(p), fp32=True)
+    assert np.array_equal(host(rpc), rpc_r) and np.array_equal(host(cic), cic_r)
+    assert bits_equal(host(valc), valc_r)
+
+
+def test_galerkin_fp32_long_rows():
+    """Coarse rows gathering > 256 fine entries take the block-per-row kernel."""
+    import scipy.sparse as sp
+    n = 1500
+    rng = np.random.default_rng(5)
+    A = P.to_scipy(*P.random_spd(n, 4.0, seed=3)).tolil()
+    for h in (0, 1):
+        nb = rng.choice(np.arange(2, n), size=600, replace=False)
+        A[h, nb] = -0.01
+        A[nb, h] = -0.01
+    A = sp.csr_matrix(A)
+    A = A + sp.diags(np.asarray(abs(A).sum(axis=1)).ravel())
+    A = sp.csr_matrix(0.5 * (A + A.T))
+    A.sort_indices()
+    mat = (A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data)
+    v = np.ones(n)
+    w = oracle.edge_weights(*mat, v)
+    agg, nc, _, _ = oracle.aggregate(oracle.greedy_match(mat[0], mat[1], w))
+    p, _ = oracle.prolongator(agg, nc, v)
+    rpc_r, cic_r, valc_r = oracle.galerkin(*mat, agg, nc, p, fp32=True)
+    rpc, cic, valc = B.cwm_galerkin(*csr_dev(*mat), nc, dev(agg), dev(p), fp32=True)
+    assert np.diff(rpc_r).max() > 256
+    assert np.array_equal(host(cic), cic_r) and bits_equal(host(valc), valc_r)
+
+
+HIER = [("poisson3d_20", lambda: P.poisson3d(20), None, 3, 20),
+        ("lognormal_20", lambda: P.lognormal_diffusion(20, seed=2), None, 3, 30),
+        ("rand_d7", lambda: P.random_spd(6000, 7.0, seed=21), None, 2, 40),
+        ("elasticity_8", lambda: P.elasticity_q1(8), "comp", 2, 50)]
+
+
+@pytest.mark.parametrize("from_level", [1, 2])
+@pytest.mark.parametrize("case", HIER, ids=[c[0] for c in HIER])
+def test_hierarchy_fp32_galerkin_bit_exact(case, from_level):
+    name, gen, vkind, sweeps, cmax = case
+    mat = gen()
+    n = len(mat[0]) - 1
+    v = P.smooth_vector_components(n, seed=2) if vkind == "comp" else np.ones(n)
+    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax, galerkin_fp32_from=from_level)
+    h = B.amg_setup(*csr_dev(*mat), dev(v), B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax,
+                                                                galerkin_fp32_from=from_level))
+    try:
+        assert B.amg_num_levels(h) == H.nl
+        for k in range(H.nl):
+            got, ref = B.amg_level_export(h, k), H.level(k)
+            assert np.array_equal(host(got["rp"]), ref["rp"]) and np.array_equal(host(got["ci"]), ref["ci"])
+            assert bits_equal(host(got["val"]), ref["val"])
+            assert bits_equal(host(got["v"]), ref["v"])
+            if k < H.nl - 1:
+                assert np.array_equal(host(got["agg"]), ref["agg"])
+                assert bits_equal(host(got["p"]), ref["p"])
+    finally:
+        h.free()
+
+
+@pytest.mark.parametrize("vfp32", [0, 1])
+def test_pcg_fp32_galerkin_vs_float64_oracle(vfp32):
+    """Lognormal diffusion 24^3: FCG on the binary32-Galerkin hierarchy takes the oracle's
+    iterations on the same hierarchy (within one, three with the float32 V-cycle) and at
+    most two more than on the float64 hierarchy; the coarse operators differ from the
+    float64 ones by float rounding where the patterns coincide."""
+    mat = P.lognormal_diffusion(24, seed=4)
+    n = len(mat[0]) - 1
+    v = np.ones(n)
+    xs, b = P.manufactured_rhs(*mat, seed=3)
+    H32 = oracle.Hierarchy(*mat, v, sweeps=3, coarse_max=100, galerkin_fp32_from=1, stall_ratio=1.2)
+    H64 = oracle.Hierarchy(*mat, v, sweeps=3, coarse_max=100, stall_ratio=1.2)
+    it32 = H32.pcg(b, rtol=1e-8, itmax=500)[2]
+    it64 = H64.pcg(b, rtol=1e-8, itmax=500)[2]
+    prm = B.amg_default_params(sweeps_per_level=3, coarse_max=100, galerkin_fp32_from=1, stall_ratio=1.2,
+                               vcycle_fp32=vfp32)
+    h = B.amg_setup(*csr_dev(*mat), dev(v), prm)
+    try:
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8, itmax=500)
+        assert st == B.AMG_OK and info["rel_res_true"] <= 2e-8
+        assert it32 - 1 <= info["iters"] <= it32 + (3 if vfp32 else 1)
+        assert info["iters"] <= it64 + 2 + (2 if vfp32 else 0)
+        assert np.linalg.norm(host(x) - xs) / np.linalg.norm(xs) < 1e-5
+        compared = 0
+        for k in range(1, min(H64.nl, B.amg_num_levels(h))):
+            got, ref = B.amg_level_export(h, k), H64.level(k)
+            if not (np.array_equal(host(got["rp"]), ref["rp"]) and np.array_equal(host(got["ci"]), ref["ci"])):
+                break
+            gv = host(got["val"])
+            assert np.abs(gv - ref["val"]).max() <= 1e-5 * np.abs(ref["val"]).max()
+            compared += 1
+        assert compared >= 1
+    finally:
+        h.free()
+
+
+def test_poisson128_fp32_galerkin_closed_form():
+    """3D Poisson 128^3 (the benchmark workload) with every coarse operator from the binary32
+    product: the closed-form structure is kept (2x2x2 cubes, 5 levels) and the values sit
+    within 27u per level of 2^-k L_7; FCG converges in the float64 hierarchy's count +-1."""
+    mat = P.poisson3d(128)
+    n = len(mat[0]) - 1
+    prm = B.amg_default_params(sweeps_per_level=3, coarse_max=1000, galerkin_fp32_from=1, check_input=0)
+    h = B.amg_setup(*csr_dev(*mat), dev(np.ones(n)), prm)
+    try:
+        sizes = [B.amg_level_info(h, k)[:2] for k in range(B.amg_num_levels(h))]
+        assert sizes == [(m ** 3, 7 * m ** 3 - 6 * m ** 2) for m in (128, 64, 32, 16, 8)]
+        for k in range(1, len(sizes)):
+            L = B.amg_level_export(h, k)
+            m = 128 >> k
+            rp, ci, val = host(L["rp"]), host(L["ci"]), host(L["val"])
+            rows = np.repeat(np.arange(m ** 3), np.diff(rp))
+            ref = np.where(ci == rows, 6.0, -1.0) * 0.5 ** k
+            assert np.all(np.abs(val - ref) <= k * 27 * 2.0 ** -24 * np.abs(ref))
+            assert np.array_equal(val, val.astype(np.float32).astype(np.float64))
+        xs, b = P.manufactured_rhs(*mat, seed=0)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8)
+        assert st == B.AMG_OK and info["rel_res_true"] <= 2e-8 and abs(info["iters"] - 35) <= 1
+    finally:
+        h.free()
