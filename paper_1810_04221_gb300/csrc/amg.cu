@@ -23,6 +23,7 @@ struct Level {
   int n = 0;
   long long nnz = 0;
   int tile = 8;
+  int max_row = 0;  // longest row (selects the solve kernels: row_blocks_for)
   DBuf<int> rp, ci;
   DBuf<double> val, v, diag, dl1, dinv;
   DBuf<float> val32, dinv32;
@@ -43,13 +44,13 @@ struct Level {
   CsrView<double> view64() const {
     CsrView<double> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val.get(); a.tile = tile;
-    a.rb = row_blocks_for(n, nnz);
+    a.rb = row_blocks_for(n, nnz, max_row);
     return a;
   }
   CsrView<float> view32() const {
     CsrView<float> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get(); a.tile = tile;
-    a.rb = row_blocks_for(n, nnz);
+    a.rb = row_blocks_for(n, nnz, max_row);
     return a;
   }
 };
@@ -58,6 +59,7 @@ struct Level {
 struct SweepOut {
   int n = 0;
   long long nnz = 0;
+  int max_row = 0;
   DBuf<int> rp, ci, agg;
   DBuf<double> val, diag, dl1, v, p;
 };
@@ -253,9 +255,12 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
                            h->err.get(), s));
     CWM_TRY(galerkin_fill(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(),
                           o.ci.get(), o.val.get(), o.diag.get(), nullptr, gw, fp32_galerkin, h->err.get(), s));
+    CWM_TRY(max_row_length(nc, o.rp.get(), misc.get() + 3, s));
     CWM_CUDA(cudaMemcpyAsync(h->box.ints + 4, o.rp.get() + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CWM_CUDA(cudaMemcpyAsync(h->box.ints + 5, misc.get() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
     CWM_TRY(read_err(h, "amg_setup (Galerkin)"));
     o.nnz = h->box.ints[4];
+    o.max_row = h->box.ints[5];
     sw.push_back(std::move(o));
     SweepOut &last = sw.back();
     cn = last.n;
@@ -289,7 +294,8 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   Level C;
   C.n = last.n;
   C.nnz = last.nnz;
-  C.tile = tile_for_mean(C.n ? (double)C.nnz / C.n : 1.0);
+  C.max_row = last.max_row;
+  C.tile = tile_for_rows(C.n ? (double)C.nnz / C.n : 1.0, C.max_row);
   C.rp = std::move(last.rp);
   C.ci = std::move(last.ci);
   C.val = std::move(last.val);
@@ -577,8 +583,8 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   }
   retain_pool_memory();
   CWM_TRY(h->box.init());
-  CWM_TRY(h->err.alloc(1, s));
-  CWM_CUDA(cudaMemsetAsync(h->err.get(), 0, sizeof(int), s));
+  CWM_TRY(h->err.alloc(2, s));  // [0] error bits, [1] scratch for one device -> host int
+  CWM_CUDA(cudaMemsetAsync(h->err.get(), 0, 2 * sizeof(int), s));
 
   h->lev.emplace_back();
   Level &L0 = h->lev[0];
@@ -602,8 +608,12 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
     CWM_TRY(read_err(h, "amg_setup (input check)"));
   }
   CWM_TRY(extract_diag(n, L0.rp.get(), L0.ci.get(), L0.val.get(), L0.diag.get(), h->err.get(), s));
-  CWM_TRY(l1_norms(L0.view64(), L0.dl1.get(), s));
+  CWM_TRY(max_row_length(n, L0.rp.get(), h->err.get() + 1, s));
+  CWM_CUDA(cudaMemcpyAsync(h->box.ints + 5, h->err.get() + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   CWM_TRY(read_err(h, "amg_setup (diagonal)"));
+  L0.max_row = h->box.ints[5];
+  L0.tile = tile_for_rows((double)nnz / n, L0.max_row);
+  CWM_TRY(l1_norms(L0.view64(), L0.dl1.get(), s));
 
   while ((int)h->lev.size() < P.max_levels && h->lev.back().n > P.coarse_max) {
     bool made = false;

@@ -136,6 +136,15 @@ inline int tile_for_mean(double mean) {
   return 32;
 }
 
+// Sub-warp width for the solve kernels of a level: wide enough for the mean row, and for
+// the longest row to take at most ~8 entries per lane (a long row on one thread is a
+// chain of dependent gathers that sets the time of a small level).
+inline int tile_for_rows(double mean, int max_row) {
+  const int t_max = max_row <= 32 ? 4 : max_row <= 64 ? 8 : max_row <= 128 ? 16 : 32;
+  const int t_mean = tile_for_mean(mean);
+  return t_max > t_mean ? t_max : t_mean;
+}
+
 // ---------------------------------------------------------------- scans ----
 // out[0..n] = exclusive prefix sums of in[0..n) with out[n] = total (int32; the total
 // must fit).  scratch: at least scan_scratch_ints(n) ints.

@@ -197,9 +197,30 @@ static int rb_grid(long long n) { return (int)((n + kRB - 1) / kRB); }
 #ifndef CWM_RB_MIN_BLOCKS_PER_SM
 #define CWM_RB_MIN_BLOCKS_PER_SM 8
 #endif
-bool row_blocks_for(int n, long long nnz) {
+#ifndef CWM_RB_MAX_ROW
+#define CWM_RB_MAX_ROW 64
+#endif
+bool row_blocks_for(int n, long long nnz, int max_row) {
   if (n <= 0) return true;
-  return (double)nnz / n <= CWM_RB_MAX_MEAN || rb_grid(n) >= (long long)num_sms() * CWM_RB_MIN_BLOCKS_PER_SM;
+  if (rb_grid(n) >= (long long)num_sms() * CWM_RB_MIN_BLOCKS_PER_SM) return true;
+  return (double)nnz / n <= CWM_RB_MAX_MEAN && max_row <= CWM_RB_MAX_ROW;
+}
+
+__global__ void k_max_row(int n, const int *__restrict__ rp, int *out) {
+  int m = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, rp[i + 1] - rp[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+amg_status max_row_length(int n, const int *rp, int *d_out, cudaStream_t s) {
+  CWM_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int), s));
+  if (n <= 0) return AMG_OK;
+  k_max_row<<<grid_for(n, kBlock, num_sms() * 4), kBlock, 0, s>>>(n, rp, d_out);
+  CWM_LAUNCH();
+  return AMG_OK;
 }
 
 // Block sums of up to three values per thread with few FP64 instructions (blockDim ==

@@ -14,15 +14,18 @@ struct CsrView {
   const int *rp = nullptr;
   const int *ci = nullptr;
   const V *val = nullptr;
-  int tile = 8;  // sub-warp width chosen from the mean row length
+  int tile = 8;  // sub-warp width chosen from the row lengths (tile_for_rows)
   bool rb = true;  // row-block kernels (else a sub-warp tile per row): row_blocks_for()
 };
 
 // Row-block kernels (a thread per row, CSR chunks staged in shared memory) suit short rows,
-// or levels with enough row blocks to fill the GPU; a level with long rows and few row
-// blocks (coarse vector-PDE operators) leaves most threads of a row block idle and takes
-// a sub-warp tile per row instead.
-bool row_blocks_for(int n, long long nnz);
+// or levels with enough row blocks to fill the GPU; a small level with long rows (coarse
+// vector-PDE operators, or a few long rows left by strongly varying coefficients) leaves
+// most threads of a row block idle behind one thread's long row, and takes a sub-warp tile
+// per row instead.  max_row: the longest row (0: unknown, decided by the mean alone).
+bool row_blocks_for(int n, long long nnz, int max_row);
+// *d_out = the longest row of the CSR pattern rp (device int; asynchronous)
+amg_status max_row_length(int n, const int *rp, int *d_out, cudaStream_t s);
 
 // Largest coarsest level solved by the one-block kernel (x kept in shared memory).
 constexpr int kCoarseBlockMax = 2048;
