@@ -22,8 +22,7 @@ namespace {
 struct Level {
   int n = 0;
   long long nnz = 0;
-  int tile = 8;
-  int max_row = 0;  // longest row (selects the solve kernels: row_blocks_for)
+  int max_row = 0;  // longest row (selects the solve kernels: row_kernel_shape)
   DBuf<int> rp, ci;
   DBuf<double> val, v, diag, dl1, dinv;
   DBuf<float> val32, dinv32;
@@ -43,14 +42,14 @@ struct Level {
 
   CsrView<double> view64() const {
     CsrView<double> a;
-    a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val.get(); a.tile = tile;
-    a.rb = row_blocks_for(n, nnz, max_row);
+    a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val.get();
+    row_kernel_shape(n, nnz, max_row, true, &a.rb, &a.tile);
     return a;
   }
   CsrView<float> view32() const {
     CsrView<float> a;
-    a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get(); a.tile = tile;
-    a.rb = row_blocks_for(n, nnz, max_row);
+    a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get();
+    row_kernel_shape(n, nnz, max_row, false, &a.rb, &a.tile);
     return a;
   }
 };
@@ -295,7 +294,6 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   C.n = last.n;
   C.nnz = last.nnz;
   C.max_row = last.max_row;
-  C.tile = tile_for_rows(C.n ? (double)C.nnz / C.n : 1.0, C.max_row);
   C.rp = std::move(last.rp);
   C.ci = std::move(last.ci);
   C.val = std::move(last.val);
@@ -590,7 +588,6 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   Level &L0 = h->lev[0];
   L0.n = n;
   L0.nnz = nnz;
-  L0.tile = tile_for_mean((double)nnz / n);
   CWM_TRY(L0.rp.alloc((size_t)n + 1, s));
   CWM_TRY(L0.ci.alloc(nnz, s));
   CWM_TRY(L0.val.alloc(nnz, s));
@@ -612,7 +609,6 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   CWM_CUDA(cudaMemcpyAsync(h->box.ints + 5, h->err.get() + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   CWM_TRY(read_err(h, "amg_setup (diagonal)"));
   L0.max_row = h->box.ints[5];
-  L0.tile = tile_for_rows((double)nnz / n, L0.max_row);
   CWM_TRY(l1_norms(L0.view64(), L0.dl1.get(), s));
 
   while ((int)h->lev.size() < P.max_levels && h->lev.back().n > P.coarse_max) {
@@ -669,7 +665,7 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   CWM_TRY(h->vv.alloc(n, s));
   CWM_TRY(h->q.alloc(n, s));
   const int nb = fcg_partial_blocks(n);
-  CWM_TRY(h->part.alloc(3 * (size_t)nb, s));
+  CWM_TRY(h->part.alloc(3 * (size_t)fcg_dots_blocks_max(n, nnz), s));
   // part2 takes the partial sums of sqnorm_partials and of fcg_update, whose grids differ
   CWM_TRY(h->part2.alloc((size_t)std::max(nb, fcg_update_blocks(n)), s));
   CWM_TRY(h->scal.alloc(kFcgSlots, s));

@@ -253,6 +253,11 @@ amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, cons
 #ifndef CWM_SUITOR_ENTRIES_PER_LANE
 #define CWM_SUITOR_ENTRIES_PER_LANE 1
 #endif
+// Vertex order of the proposal tiles: 0 = strided (tile t takes t, t + #tiles, ...),
+// 1 = contiguous (tile t takes a block of consecutive vertices).
+#ifndef CWM_SUITOR_ORDER
+#define CWM_SUITOR_ORDER 0
+#endif
 // Sec. 3.1.  S[x] = (weight bits, suitor + 1) packed in 16 bytes; weights are positive
 // doubles, whose bit patterns order like their values, so the 128-bit pair compares
 // lexicographically as (weight, suitor index).  A proposer u beats the current suitor s
@@ -299,7 +304,10 @@ __global__ void __launch_bounds__(256) k_suitor(int n, const int *__restrict__ r
   const int lane = tile.thread_rank();
   const long long tile0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
   const long long ntiles = (long long)gridDim.x * blockDim.x / T;
-  for (long long u = tile0; u < n; u += ntiles) {
+  const long long per_tile = (n + ntiles - 1) / ntiles;
+  for (long long i = 0; i < per_tile; ++i) {
+    const long long u = CWM_SUITOR_ORDER == 1 ? tile0 * per_tile + i : tile0 + i * ntiles;
+    if (u >= n) break;
     int current = (int)u;
     long long steps = 0;
     for (;;) {

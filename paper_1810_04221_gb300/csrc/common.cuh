@@ -137,10 +137,15 @@ inline int tile_for_mean(double mean) {
 }
 
 // Sub-warp width for the solve kernels of a level: wide enough for the mean row, and for
-// the longest row to take at most ~8 entries per lane (a long row on one thread is a
-// chain of dependent gathers that sets the time of a small level).
+// the longest row to take at most CWM_TILE_MAX_PER_LANE entries per lane (a long row on
+// few lanes is a chain of gathers that sets the time of a small level; 32 measured best
+// against 8 and 16, the row dot keeping four gathers per lane in flight).
+#ifndef CWM_TILE_MAX_PER_LANE
+#define CWM_TILE_MAX_PER_LANE 32
+#endif
 inline int tile_for_rows(double mean, int max_row) {
-  const int t_max = max_row <= 32 ? 4 : max_row <= 64 ? 8 : max_row <= 128 ? 16 : 32;
+  const int e = CWM_TILE_MAX_PER_LANE;
+  const int t_max = max_row <= 4 * e ? 4 : max_row <= 8 * e ? 8 : max_row <= 16 * e ? 16 : 32;
   const int t_mean = tile_for_mean(mean);
   return t_max > t_mean ? t_max : t_mean;
 }

@@ -17,7 +17,18 @@ __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int 
   V s = V(0);
   if (active && x) {
     const int b = rp[row], e = rp[row + 1];
-    for (int k = b + lane; k < e; k += T) s += val[k] * __ldg(x + ci[k]);
+    int k = b + lane;
+    // four entries per lane in flight: a long row is a chain of gathers otherwise
+    for (; k + 3 * T < e; k += 4 * T) {
+      const int j0 = ci[k], j1 = ci[k + T], j2 = ci[k + 2 * T], j3 = ci[k + 3 * T];
+      const V a0 = val[k], a1 = val[k + T], a2 = val[k + 2 * T], a3 = val[k + 3 * T];
+      const V x0 = __ldg(x + j0), x1 = __ldg(x + j1), x2 = __ldg(x + j2), x3 = __ldg(x + j3);
+      s = fma(a0, x0, s);
+      s = fma(a1, x1, s);
+      s = fma(a2, x2, s);
+      s = fma(a3, x3, s);
+    }
+    for (; k < e; k += T) s = fma(val[k], __ldg(x + ci[k]), s);
   }
 #pragma unroll
   for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
@@ -200,10 +211,21 @@ static int rb_grid(long long n) { return (int)((n + kRB - 1) / kRB); }
 #ifndef CWM_RB_MAX_ROW
 #define CWM_RB_MAX_ROW 64
 #endif
-bool row_blocks_for(int n, long long nnz, int max_row) {
-  if (n <= 0) return true;
-  if (rb_grid(n) >= (long long)num_sms() * CWM_RB_MIN_BLOCKS_PER_SM) return true;
-  return (double)nnz / n <= CWM_RB_MAX_MEAN && max_row <= CWM_RB_MAX_ROW;
+#ifndef CWM_TILE64_MEAN_PER_LANE
+#define CWM_TILE64_MEAN_PER_LANE 24
+#endif
+void row_kernel_shape(int n, long long nnz, int max_row, bool fp64, bool *rb, int *tile) {
+  const double mean = n > 0 ? (double)nnz / n : 1.0;
+  const bool short_rows = mean <= CWM_RB_MAX_MEAN && max_row <= CWM_RB_MAX_ROW;
+  if (fp64) {
+    *rb = n <= 0 || short_rows;
+    int t = 4;
+    while (t < 32 && (mean > (double)CWM_TILE64_MEAN_PER_LANE * t || max_row > CWM_TILE_MAX_PER_LANE * t)) t <<= 1;
+    *tile = t;
+  } else {
+    *rb = n <= 0 || short_rows || rb_grid(n) >= (long long)num_sms() * CWM_RB_MIN_BLOCKS_PER_SM;
+    *tile = tile_for_rows(mean, max_row);
+  }
 }
 
 __global__ void k_max_row(int n, const int *__restrict__ rp, int *out) {
@@ -779,35 +801,6 @@ int fcg_partial_blocks(int n) {
 constexpr int kUpdChunk = 8 * kRB;  // entries per fcg_update block
 int fcg_update_blocks(int n) { return (int)(((n > 0 ? n : 1) + kUpdChunk - 1LL) / kUpdChunk); }
 
-// v = A w fused with the three dot products of Algorithm 3 (w is read once per row).
-template <int T>
-__global__ void __launch_bounds__(kBlock)
-    k_spmv_dots(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ val,
-                const double *__restrict__ w, const double *__restrict__ r, const double *__restrict__ q,
-                double *__restrict__ v, double *__restrict__ part) {
-  double sa = 0.0, sb = 0.0, sg = 0.0;
-  CWM_TILE_LOOP(T, n) {
-    const long long row = base + sub;
-    const bool active = row < n;
-    const double dot = tile_row_dot<double, T>(rp, ci, val, w, row, active, lane);
-    if (active && lane == 0) {
-      v[row] = dot;
-      const double wi = w[row];
-      sa += wi * r[row];
-      sb += wi * dot;
-      if (q) sg += wi * q[row];
-    }
-  }
-  const double ta = block_sum(sa);
-  const double tb = block_sum(sb);
-  const double tg = block_sum(sg);
-  if (threadIdx.x == 0) {
-    part[3 * blockIdx.x + 0] = ta;
-    part[3 * blockIdx.x + 1] = tb;
-    part[3 * blockIdx.x + 2] = tg;
-  }
-}
-
 // The block that finishes last (atomic ticket after a fence) reduces every block's partial
 // sums in block order -- a fixed order, so the result does not depend on scheduling -- and
 // resets the ticket for the next launch.
@@ -895,10 +888,70 @@ __global__ void __launch_bounds__(kRB)
   }
 }
 
+// Same with a sub-warp tile per row (levels on sub-warp tiles, see row_blocks_for).
+template <int T>
+__global__ void __launch_bounds__(kBlock)
+    k_spmv_dots_tile(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ val,
+                     const double *__restrict__ w, const double *__restrict__ r, const double *__restrict__ q,
+                     double *__restrict__ v, double *__restrict__ part, double *scal, unsigned *tick, int first) {
+  double sa = 0.0, sb = 0.0, sg = 0.0;
+  CWM_TILE_LOOP(T, n) {
+    const long long row = base + sub;
+    const bool active = row < n;
+    const double dot = tile_row_dot<double, T>(rp, ci, val, w, row, active, lane);
+    if (active && lane == 0) {
+      v[row] = dot;
+      const double wi = w[row];
+      sa = fma(wi, r[row], sa);
+      sb = fma(wi, dot, sb);
+      if (q) sg = fma(wi, q[row], sg);
+    }
+  }
+  const double in3[3] = {sa, sb, sg};
+  double t3[3];
+  block_sums<3>(in3, t3);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x + 0] = t3[0];
+    part[3 * blockIdx.x + 1] = t3[1];
+    part[3 * blockIdx.x + 2] = t3[2];
+  }
+  if (last_block(tick)) {
+    fcg_scalars_from(gridDim.x, part, scal, first);
+    if (threadIdx.x == 0) *tick = 0u;
+  }
+}
+
+#ifndef CWM_DOTS_RB_MAX_MEAN
+#define CWM_DOTS_RB_MAX_MEAN 1e30
+#endif
+#ifndef CWM_DOTS_ENTRIES_PER_BLOCK
+#define CWM_DOTS_ENTRIES_PER_BLOCK 8192
+#endif
+// Row-block grid of spmv_dots: kDotsBlocksPerSm per SM, or more when that would give a block
+// more than ~8K nonzeros (long rows: a block's row blocks are walked one after the other).
+int fcg_dots_blocks(int n, long long nnz) {
+  const long long rb = rb_grid(n > 0 ? n : 1);
+  long long g = (long long)num_sms() * kDotsBlocksPerSm;
+  const long long by_nnz = nnz / CWM_DOTS_ENTRIES_PER_BLOCK;
+  if (by_nnz > g) g = by_nnz;
+  return (int)(rb < g ? rb : g);
+}
+int fcg_dots_blocks_max(int n, long long nnz) {
+  const int a = fcg_dots_blocks(n, nnz), b = num_sms() * 8;
+  return a > b ? a : b;
+}
+
 amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const double *r, const double *q,
                              double *v, double *part, double *scal, unsigned *tick, int first, cudaStream_t s) {
   CWM_TRACE("spmv_dots", 4.0 * (A.n + 1) + 12.0 * A.nnz + (q ? 32.0 : 24.0) * A.n, s);
-  k_spmv_dots_rb<<<fcg_partial_blocks(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r, q, v, part, scal, tick, first);
+  if (A.rb && (A.n == 0 || (double)A.nnz / A.n <= CWM_DOTS_RB_MAX_MEAN)) {
+    k_spmv_dots_rb<<<fcg_dots_blocks(A.n, A.nnz), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r, q, v, part, scal, tick,
+                                                          first);
+  } else {
+    // at most num_sms() * 8 blocks (rows_grid), within fcg_dots_blocks_max
+    CWM_DISPATCH_T(A.tile, (k_spmv_dots_tile<kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r,
+                                                                                    q, v, part, scal, tick, first)));
+  }
   CWM_LAUNCH();
   return AMG_OK;
 }

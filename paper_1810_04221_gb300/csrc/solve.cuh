@@ -18,12 +18,15 @@ struct CsrView {
   bool rb = true;  // row-block kernels (else a sub-warp tile per row): row_blocks_for()
 };
 
-// Row-block kernels (a thread per row, CSR chunks staged in shared memory) suit short rows,
-// or levels with enough row blocks to fill the GPU; a small level with long rows (coarse
-// vector-PDE operators, or a few long rows left by strongly varying coefficients) leaves
-// most threads of a row block idle behind one thread's long row, and takes a sub-warp tile
-// per row instead.  max_row: the longest row (0: unknown, decided by the mean alone).
-bool row_blocks_for(int n, long long nnz, int max_row);
+// Shape of a level's solve kernels: row blocks (a thread per row, CSR chunks staged in
+// shared memory) or a sub-warp tile of *tile lanes per row.  Row blocks suit short rows.
+// With long rows a chunk holds few rows, so few threads (spread over two warps) work while
+// the rest wait at the block barrier; in FP64, which GB300 issues per warp instruction at
+// a low rate, the half-empty warps double the cost, so FP64 long rows take narrow tiles
+// (about a dozen entries per lane, few shuffle steps per row).  FP32 keeps row blocks on
+// levels large enough to fill the GPU and takes wide tiles on small ones.  max_row: the
+// longest row (0: unknown).
+void row_kernel_shape(int n, long long nnz, int max_row, bool fp64, bool *rb, int *tile);
 // *d_out = the longest row of the CSR pattern rp (device int; asynchronous)
 amg_status max_row_length(int n, const int *rp, int *d_out, cudaStream_t s);
 
@@ -111,7 +114,9 @@ amg_status residual(const CsrView<double> &A, const double *b, const double *x, 
 
 // FCG device scalars (one array of doubles on the device).
 enum FcgSlot { kAlpha = 0, kBeta, kGamma, kRho, kRhoPrev, kCoef, kStep, kRR, kBB, kFlags, kFcgSlots };
-int fcg_partial_blocks(int n);   // partial sums written by spmv_dots and sqnorm_partials
+int fcg_partial_blocks(int n);   // partial sums written by sqnorm_partials
+int fcg_dots_blocks(int n, long long nnz);      // row-block grid of spmv_dots
+int fcg_dots_blocks_max(int n, long long nnz);  // largest spmv_dots grid of either form (part: 3 per block)
 int fcg_update_blocks(int n);    // partial sums written by fcg_update
 // v = A w with per-block partial sums of w.r, w.v, w.q (q may be NULL) into part[3 * nb];
 // the last block to finish turns them into alpha, beta, gamma, rho, coef = gamma/rho_prev
