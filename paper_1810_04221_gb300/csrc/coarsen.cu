@@ -253,8 +253,11 @@ amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, cons
 #ifndef CWM_SUITOR_ENTRIES_PER_LANE
 #define CWM_SUITOR_ENTRIES_PER_LANE 1
 #endif
-// Vertex order of the proposal tiles: 0 = strided (tile t takes t, t + #tiles, ...),
-// 1 = contiguous (tile t takes a block of consecutive vertices).
+// Vertex order of the proposal tiles: 0 = strided (tile t takes t, t + #tiles, ...: the
+// proposals sweep the vertices in ascending order), 1 = contiguous (tile t takes a block of
+// consecutive vertices).  Under weight ties the order decides how long the displacement
+// cascades get: on 3D Poisson 128^3 the first sweep takes 1.8-4.4 ms strided, 123 ms
+// contiguous, and 77 ms strided in descending order (measured).
 #ifndef CWM_SUITOR_ORDER
 #define CWM_SUITOR_ORDER 0
 #endif

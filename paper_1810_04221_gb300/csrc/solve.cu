@@ -816,13 +816,28 @@ __device__ __forceinline__ bool last_block(unsigned *tick) {
   return s_last;
 }
 
-__device__ __forceinline__ void fcg_scalars_from(int nb, const double *part, double *scal, int first) {
-  double a = 0.0, b = 0.0, g = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    a += __ldcg(part + 3 * i);
-    b += __ldcg(part + 3 * i + 1);
-    g += __ldcg(part + 3 * i + 2);
+// Sum of part[stride * i + c] over i = threadIdx.x, threadIdx.x + blockDim.x, ... < nb, in
+// that order; the L2 loads of four iterations are issued before their adds (this runs on
+// the critical path, in the last block, after every other block has finished).
+template <int STRIDE, int C>
+__device__ __forceinline__ double strided_sum(int nb, const double *part) {
+  double a = 0.0;
+  int i = threadIdx.x;
+  const int bd = blockDim.x;
+  for (; i + 3 * bd < nb; i += 4 * bd) {
+    const double t0 = __ldcg(part + STRIDE * i + C), t1 = __ldcg(part + STRIDE * (i + bd) + C);
+    const double t2 = __ldcg(part + STRIDE * (i + 2 * bd) + C), t3 = __ldcg(part + STRIDE * (i + 3 * bd) + C);
+    a += t0;
+    a += t1;
+    a += t2;
+    a += t3;
   }
+  for (; i < nb; i += bd) a += __ldcg(part + STRIDE * i + C);
+  return a;
+}
+
+__device__ __forceinline__ void fcg_scalars_from(int nb, const double *part, double *scal, int first) {
+  double a = strided_sum<3, 0>(nb, part), b = strided_sum<3, 1>(nb, part), g = strided_sum<3, 2>(nb, part);
   {
     const double in3[3] = {a, b, g};
     double o3[3];
@@ -1052,8 +1067,7 @@ __global__ void __launch_bounds__(kBlock)
     if (threadIdx.x == 0) part[blockIdx.x] = o1[0];
   }
   if (last_block(tick)) {
-    double a = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += __ldcg(part + b);
+    const double a = strided_sum<1, 0>((int)gridDim.x, part);
     const double in1[1] = {a};
     double o1[1];
     block_sums<1>(in1, o1);
