@@ -44,12 +44,14 @@ struct Level {
     CsrView<double> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val.get();
     row_kernel_shape(n, nnz, max_row, true, &a.rb, &a.tile);
+    a.max_row = max_row;
     return a;
   }
   CsrView<float> view32() const {
     CsrView<float> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get();
     row_kernel_shape(n, nnz, max_row, false, &a.rb, &a.tile);
+    a.max_row = max_row;
     return a;
   }
 };

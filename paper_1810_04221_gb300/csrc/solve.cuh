@@ -15,7 +15,8 @@ struct CsrView {
   const int *ci = nullptr;
   const V *val = nullptr;
   int tile = 8;  // sub-warp width chosen from the row lengths (tile_for_rows)
-  bool rb = true;  // row-block kernels (else a sub-warp tile per row): row_blocks_for()
+  bool rb = true;  // row-block kernels (else a sub-warp tile per row): row_kernel_shape()
+  int max_row = 0;  // longest row (0: unknown)
 };
 
 // Shape of a level's solve kernels: row blocks (a thread per row, CSR chunks staged in
