@@ -274,6 +274,7 @@ __device__ __forceinline__ void block_sums(const double (&in)[NV], double (&out)
 // ------------------------------------------------------------ elementwise ----
 template <class V>
 __global__ void k_scale(int n, const V *__restrict__ dinv, const V *__restrict__ b, V *__restrict__ y) {
+  pdl_begin();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = dinv[i] * b[i];
 }
@@ -282,7 +283,7 @@ template <class V>
 amg_status scale(int n, const V *dinv, const V *b, V *y, cudaStream_t s) {
   if (n == 0) return AMG_OK;
   CWM_TRACE("scale", 3.0 * sizeof(V) * n, s);
-  k_scale<V><<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, dinv, b, y);
+  CWM_CUDA(launch_pdl(k_scale<V>, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, dinv, b, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -290,6 +291,7 @@ amg_status scale(int n, const V *dinv, const V *b, V *y, cudaStream_t s) {
 template <class V>
 __global__ void k_prolong(int n, const int *__restrict__ agg, const V *__restrict__ p, const V *__restrict__ xc,
                           const V *__restrict__ x, V *__restrict__ y) {
+  pdl_begin();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const V base = x ? x[i] : V(0);
     y[i] = base + p[i] * __ldg(xc + agg[i]);
@@ -300,7 +302,7 @@ template <class V>
 amg_status prolong(int n, const int *agg, const V *p, const V *xc, const V *x, V *y, cudaStream_t s) {
   if (n == 0) return AMG_OK;
   CWM_TRACE("prolong", (4.0 + (x ? 3.0 : 2.0) * sizeof(V)) * n, s);
-  k_prolong<V><<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, agg, p, xc, x, y);
+  CWM_CUDA(launch_pdl(k_prolong<V>, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, agg, p, xc, x, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -311,6 +313,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
                                                    const V *__restrict__ val, const V *__restrict__ dinv,
                                                    const V *__restrict__ b, const V *__restrict__ x,
                                                    V *__restrict__ y) {
+  pdl_begin();
   CWM_TILE_LOOP(T, n) {
     const long long row = base + sub;
     const bool active = row < n;
@@ -324,6 +327,7 @@ __global__ void __launch_bounds__(kRB) k_jacobi_rb(int n, const int *__restrict_
                                                    const V *__restrict__ val, const V *__restrict__ dinv,
                                                    const V *__restrict__ b, const V *__restrict__ x,
                                                    V *__restrict__ y) {
+  pdl_begin();
   __shared__ RowBlockSmem<V> sm;
   const int r0 = blockIdx.x * kRB;
   const int nrows = min(kRB, n - r0);
@@ -338,9 +342,9 @@ amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V 
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("jacobi", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 4.0 * sizeof(V) * A.n, s);
   if (A.rb) {
-    k_jacobi_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, y);
+    CWM_CUDA(launch_pdl(k_jacobi_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, x, y));
   } else {
-    CWM_DISPATCH_T(A.tile, (k_jacobi<V, kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b,
+    CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_jacobi<V, kT>, rows_grid(A.n, kT), kBlock, 0, s, A.n, A.rp, A.ci, A.val, dinv, b,
                                                                                 x, y)));
   }
   CWM_LAUNCH();
@@ -355,6 +359,7 @@ __global__ void __launch_bounds__(kBlock)
     k_resid_restrict(int nc, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ val,
                      const int *__restrict__ mptr, const int *__restrict__ mlist, const V *__restrict__ p,
                      const V *__restrict__ b, const V *__restrict__ x, V *__restrict__ bc) {
+  pdl_begin();
   CWM_TILE_LOOP(T, nc) {
     const long long I = base + sub;
     const bool active = I < nc;
@@ -385,6 +390,7 @@ template <class V>
 __global__ void __launch_bounds__(kRB) k_resid_scaled_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                          const V *__restrict__ val, const V *__restrict__ dinv,
                                                          const V *__restrict__ b, V *__restrict__ r) {
+  pdl_begin();
   __shared__ RowBlockSmem<V> sm;
   const int r0 = blockIdx.x * kRB;
   const int nrows = min(kRB, n - r0);
@@ -403,6 +409,7 @@ __global__ void __launch_bounds__(kRB) k_prolong_jacobi_rb(int n, const int *__r
                                                            const V *__restrict__ dinv, const V *__restrict__ b,
                                                            const int *__restrict__ agg, const V *__restrict__ p,
                                                            const V *__restrict__ xc, V *__restrict__ x) {
+  pdl_begin();
   __shared__ RowBlockSmem<V> sm;
   const int r0 = blockIdx.x * kRB;
   const int nrows = min(kRB, n - r0);
@@ -420,6 +427,7 @@ __global__ void __launch_bounds__(kRB) k_prolong_jacobi_rb(int n, const int *__r
 template <class V>
 __global__ void k_prolong_scaled(int n, const int *__restrict__ agg, const V *__restrict__ p, const V *__restrict__ xc,
                                  const V *__restrict__ dinv, const V *__restrict__ b, V *__restrict__ y) {
+  pdl_begin();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = fma(p[i], __ldg(xc + agg[i]), dinv[i] * b[i]);
 }
@@ -430,11 +438,11 @@ amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, c
   if (nc == 0) return AMG_OK;
   {
     CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
-    k_resid_scaled_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, r_scratch);
+    CWM_CUDA(launch_pdl(k_resid_scaled_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, r_scratch));
     CWM_LAUNCH();
   }
   CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
-  k_restrict<V><<<grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s>>>(nc, mptr, mlist, p, r_scratch, bc);
+  CWM_CUDA(launch_pdl(k_restrict<V>, grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s, nc, mptr, mlist, p, r_scratch, bc));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -444,7 +452,7 @@ amg_status prolong_jacobi(const CsrView<V> &A, const V *dinv, const V *b, const 
                           V *x, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("prolong_jacobi", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + (5.0 * sizeof(V) + 4.0) * A.n, s);
-  k_prolong_jacobi_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, agg, p, xc, x);
+  CWM_CUDA(launch_pdl(k_prolong_jacobi_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, agg, p, xc, x));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -454,7 +462,7 @@ amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const 
                           cudaStream_t s) {
   if (n == 0) return AMG_OK;
   CWM_TRACE("prolong", (4.0 + 4.0 * sizeof(V)) * n, s);
-  k_prolong_scaled<V><<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, agg, p, xc, dinv, b, y);
+  CWM_CUDA(launch_pdl(k_prolong_scaled<V>, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, agg, p, xc, dinv, b, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -464,6 +472,7 @@ template <class V>
 __global__ void __launch_bounds__(kRB) k_resid_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                   const V *__restrict__ val, const V *__restrict__ b,
                                                   const V *__restrict__ x, V *__restrict__ r) {
+  pdl_begin();
   __shared__ RowBlockSmem<V> sm;
   const int r0 = blockIdx.x * kRB;
   const int nrows = min(kRB, n - r0);
@@ -478,6 +487,7 @@ template <class V, int T>
 __global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                      const V *__restrict__ val, const V *__restrict__ b,
                                                      const V *__restrict__ x, V *__restrict__ r) {
+  pdl_begin();
   CWM_TILE_LOOP(T, n) {
     const long long row = base + sub;
     const bool active = row < n;
@@ -487,26 +497,28 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restric
 }
 
 template <class V>
-static void launch_residual(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s) {
+static amg_status launch_residual(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s) {
   if (A.rb) {
-    k_resid_rb<V><<<rb_grid(A.n), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x, r);
+    CWM_CUDA(launch_pdl(k_resid_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, b, x, r));
   } else {
-    CWM_DISPATCH_T(A.tile, (k_residual<V, kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, b, x,
+    CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_residual<V, kT>, rows_grid(A.n, kT), kBlock, 0, s, A.n, A.rp, A.ci, A.val, b, x,
                                                                                   r)));
   }
+  return AMG_OK;
 }
 
 template <class V>
 amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
-  launch_residual<V>(A, b, x, r, s);
+  CWM_TRY(launch_residual<V>(A, b, x, r, s));
   CWM_LAUNCH();
   return AMG_OK;
 }
 
 template <class V>
 __global__ void k_add_to(int n, const V *__restrict__ x, V *__restrict__ y) {
+  pdl_begin();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] += x[i];
 }
@@ -515,7 +527,7 @@ template <class V>
 amg_status add_to(int n, const V *x, V *y, cudaStream_t s) {
   if (n == 0) return AMG_OK;
   CWM_TRACE("add", 3.0 * sizeof(V) * n, s);
-  k_add_to<V><<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, x, y);
+  CWM_CUDA(launch_pdl(k_add_to<V>, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, x, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -524,6 +536,7 @@ amg_status add_to(int n, const V *x, V *y, cudaStream_t s) {
 template <class V>
 __global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__restrict__ mlist,
                            const V *__restrict__ p, const V *__restrict__ r, V *__restrict__ bc) {
+  pdl_begin();
   for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += (long long)gridDim.x * blockDim.x) {
     const int s = mptr[I], e = mptr[I + 1];
     V acc = V(0);
@@ -541,11 +554,11 @@ amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const
   if (nc == 0) return AMG_OK;
   {
     CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
-    launch_residual<V>(A, b, x, r_scratch, s);
+    CWM_TRY(launch_residual<V>(A, b, x, r_scratch, s));
     CWM_LAUNCH();
   }
   CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
-  k_restrict<V><<<grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s>>>(nc, mptr, mlist, p, r_scratch, bc);
+  CWM_CUDA(launch_pdl(k_restrict<V>, grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s, nc, mptr, mlist, p, r_scratch, bc));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -556,7 +569,7 @@ amg_status resid_restrict(const CsrView<V> &A, int nc, const int *mptr, const in
   if (nc == 0) return AMG_OK;
   CWM_TRACE("resid_restrict", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + (3.0 * sizeof(V) + 4.0) * A.n +
                                   (4.0 + sizeof(V)) * nc, s);
-  CWM_DISPATCH_T(A.tile, (k_resid_restrict<V, kT><<<rows_grid(nc, kT), kBlock, 0, s>>>(nc, A.rp, A.ci, A.val, mptr,
+  CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_resid_restrict<V, kT>, rows_grid(nc, kT), kBlock, 0, s, nc, A.rp, A.ci, A.val, mptr,
                                                                                       mlist, p, b, x, bc)));
   CWM_LAUNCH();
   return AMG_OK;
@@ -568,6 +581,7 @@ template <class V>
 __global__ void __launch_bounds__(1024) k_coarse_block(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                        const V *__restrict__ val, const V *__restrict__ dinv,
                                                        const V *__restrict__ b, V *__restrict__ x, int sweeps) {
+  pdl_begin();
   extern __shared__ unsigned char smem_raw[];
   V *xa = reinterpret_cast<V *>(smem_raw);
   V *xb = xa + n;
@@ -591,6 +605,7 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(int n, int nnz, const int 
                                                       const int *__restrict__ ci, const V *__restrict__ val,
                                                       const V *__restrict__ dinv, const V *__restrict__ b,
                                                       V *__restrict__ x, int sweeps) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *s_val = reinterpret_cast<V *>(smem_raw);
   V *s_dinv = s_val + nnz;
@@ -646,10 +661,10 @@ amg_status coarse_solve_block(const CsrView<V> &A, const V *dinv, const V *b, V 
                                     (int)kCoarseSmemMax));
       attr[dev & 63] = true;
     }
-    k_coarse_smem<V><<<1, 1024, big, s>>>(A.n, (int)A.nnz, A.rp, A.ci, A.val, dinv, b, x, sweeps);
+    CWM_CUDA(launch_pdl(k_coarse_smem<V>, 1, 1024, big, s, A.n, (int)A.nnz, A.rp, A.ci, A.val, dinv, b, x, sweeps));
   } else {
     const size_t sm = 2 * (size_t)A.n * sizeof(V);
-    k_coarse_block<V><<<1, 1024, sm, s>>>(A.n, A.rp, A.ci, A.val, dinv, b, x, sweeps);
+    CWM_CUDA(launch_pdl(k_coarse_block<V>, 1, 1024, sm, s, A.n, A.rp, A.ci, A.val, dinv, b, x, sweeps));
   }
   CWM_LAUNCH();
   return AMG_OK;
@@ -702,6 +717,7 @@ amg_status dense_coarse_build(const CsrView<double> &A, const double *dinv, int 
 // y = X b, one warp per row of X (row-major)
 template <class V>
 __global__ void k_dense_matvec(int n, const V *__restrict__ X, const V *__restrict__ b, V *__restrict__ y) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -719,7 +735,7 @@ template <class V>
 amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t s) {
   if (n == 0) return AMG_OK;
   CWM_TRACE("coarse", (double)sizeof(V) * ((double)n * n + 2.0 * n), s);
-  k_dense_matvec<V><<<grid_for((long long)n * 32, 128, 1 << 30), 128, 0, s>>>(n, X, b, y);
+  CWM_CUDA(launch_pdl(k_dense_matvec<V>, grid_for((long long)n * 32, 128, 1 << 30), 128, 0, s, n, X, b, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -729,7 +745,7 @@ amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t 
 amg_status residual(const CsrView<double> &A, const double *b, const double *x, double *r, cudaStream_t s) {
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("residual", 4.0 * (A.n + 1) + 12.0 * A.nnz + 24.0 * A.n, s);
-  launch_residual<double>(A, b, x, r, s);
+  CWM_TRY(launch_residual<double>(A, b, x, r, s));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -872,6 +888,7 @@ __global__ void __launch_bounds__(kRB)
     k_spmv_dots_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ val,
                    const double *__restrict__ w, const double *__restrict__ r, const double *__restrict__ q,
                    double *__restrict__ v, double *__restrict__ part, double *scal, unsigned *tick, int first) {
+  pdl_begin();
   __shared__ RowBlockSmem<double> sm;
   double sa = 0.0, sb = 0.0, sg = 0.0;
   // grid-stride over row blocks: each thread accumulates its rows' contributions, so the
@@ -909,6 +926,7 @@ __global__ void __launch_bounds__(kBlock)
     k_spmv_dots_tile(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ val,
                      const double *__restrict__ w, const double *__restrict__ r, const double *__restrict__ q,
                      double *__restrict__ v, double *__restrict__ part, double *scal, unsigned *tick, int first) {
+  pdl_begin();
   double sa = 0.0, sb = 0.0, sg = 0.0;
   CWM_TILE_LOOP(T, n) {
     const long long row = base + sub;
@@ -960,11 +978,11 @@ amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const do
                              double *v, double *part, double *scal, unsigned *tick, int first, cudaStream_t s) {
   CWM_TRACE("spmv_dots", 4.0 * (A.n + 1) + 12.0 * A.nnz + (q ? 32.0 : 24.0) * A.n, s);
   if (A.rb && (A.n == 0 || (double)A.nnz / A.n <= CWM_DOTS_RB_MAX_MEAN)) {
-    k_spmv_dots_rb<<<fcg_dots_blocks(A.n, A.nnz), kRB, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r, q, v, part, scal, tick,
-                                                          first);
+    CWM_CUDA(launch_pdl(k_spmv_dots_rb, fcg_dots_blocks(A.n, A.nnz), kRB, 0, s, A.n, A.rp, A.ci, A.val, w, r, q, v, part, scal, tick,
+                                                          first));
   } else {
     // at most num_sms() * 8 blocks (rows_grid), within fcg_dots_blocks_max
-    CWM_DISPATCH_T(A.tile, (k_spmv_dots_tile<kT><<<rows_grid(A.n, kT), kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, w, r,
+    CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_spmv_dots_tile<kT>, rows_grid(A.n, kT), kBlock, 0, s, A.n, A.rp, A.ci, A.val, w, r,
                                                                                     q, v, part, scal, tick, first)));
   }
   CWM_LAUNCH();
@@ -1015,6 +1033,7 @@ __global__ void __launch_bounds__(kBlock)
     k_fcg_update(int n, const double *__restrict__ w, const double *__restrict__ v, double *__restrict__ d,
                  double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
                  double *__restrict__ scal, double *__restrict__ part, unsigned *tick, int first, int vec) {
+  pdl_begin();
   const bool broken = scal[kFlags] != 0.0;  // breakdown: leave x, r, d, q as they were
   const double coef = scal[kCoef], step = scal[kStep];
   double rr = 0.0;
@@ -1083,7 +1102,7 @@ amg_status fcg_update(int n, const double *w, const double *v, double *d, double
   CWM_TRACE("fcg_update", (first ? 64.0 : 80.0) * n, s);
   auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
   const int vec = al(w) && al(v) && al(d) && al(q) && al(x) && al(r);
-  k_fcg_update<<<fcg_update_blocks(n), kRB, 0, s>>>(n, w, v, d, q, x, r, scal, part, tick, first, vec);
+  CWM_CUDA(launch_pdl(k_fcg_update, fcg_update_blocks(n), kRB, 0, s, n, w, v, d, q, x, r, scal, part, tick, first, vec));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -1117,22 +1136,24 @@ amg_status sqnorm_partials(int n, const double *a, double *part, cudaStream_t s)
 }
 
 __global__ void k_to_float(long long n, const double *__restrict__ x, float *__restrict__ y) {
+  pdl_begin();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
 }
 __global__ void k_to_double(long long n, const float *__restrict__ x, double *__restrict__ y) {
+  pdl_begin();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
 amg_status to_float(long long n, const double *x, float *y, cudaStream_t s) {
   if (n == 0) return AMG_OK;
-  k_to_float<<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, x, y);
+  CWM_CUDA(launch_pdl(k_to_float, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, x, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
 amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
   if (n == 0) return AMG_OK;
-  k_to_double<<<grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s>>>(n, x, y);
+  CWM_CUDA(launch_pdl(k_to_double, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, x, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
