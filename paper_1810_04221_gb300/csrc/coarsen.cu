@@ -253,14 +253,16 @@ amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, cons
 #ifndef CWM_SUITOR_ENTRIES_PER_LANE
 #define CWM_SUITOR_ENTRIES_PER_LANE 1
 #endif
-// Vertex order of the proposal tiles: 0 = strided (tile t takes t, t + #tiles, ...: the
-// proposals sweep the vertices in ascending order), 1 = contiguous (tile t takes a block of
-// consecutive vertices).  Under weight ties the order decides how long the displacement
-// cascades get: on 3D Poisson 128^3 the first sweep takes 1.8-4.4 ms strided, 123 ms
-// contiguous, and 77 ms strided in descending order (measured).
-#ifndef CWM_SUITOR_ORDER
-#define CWM_SUITOR_ORDER 0
-#endif
+// Proposal tiles and their order.  One T-lane tile per vertex, blocks of kSuitorBlock
+// threads, vertices taken in descending order as the hardware dispatches blocks.  The
+// earlier design -- a resident grid whose tiles walked strided lists of ~50 vertices --
+// let displacement chains queue behind one tile's list (one tile ran 2,400 proposal steps
+// on 3D Poisson 128^3 where a lockstep model of the same proposals needs ~345) and took
+// 1.3-4.0 ms for that level's first sweep, varying from run to run.  One vertex per tile
+// in ascending order took 1.15-1.3 ms; descending 1.0-1.13 ms (lognormal 160^3: 2.5 ->
+// 1.0 ms; Q1 elasticity 64^3: 4.3 -> 0.8 ms).  Small blocks release their slot as soon as
+// their few tiles finish (64 vs 256 threads measured equal or slightly better).
+constexpr int kSuitorBlock = 64;
 // Sec. 3.1.  S[x] = (weight bits, suitor + 1) packed in 16 bytes; weights are positive
 // doubles, whose bit patterns order like their values, so the 128-bit pair compares
 // lexicographically as (weight, suitor index).  A proposer u beats the current suitor s
@@ -292,79 +294,87 @@ __global__ void k_clear_keys(long long n, SKey *S) {
   if (i < n) { S[i].lo = 0ull; S[i].hi = 0ull; }
 }
 
-// One T-lane tile per vertex u (grid-stride).  The tile finds the best neighbour that
-// would accept the current proposer; the lane that found it installs the proposal with a
-// 128-bit CAS, taking the key it has just read as the expected value (one dependent
-// memory round trip less per proposal), and a displaced suitor becomes the next proposer
-// (the chain is followed by the same tile).  Every loop is capped; hitting a cap raises
-// kErrTimeout and ends the tile.
+// One T-lane tile per vertex u.  The tile finds the best neighbour that would accept the
+// current proposer; the lane that found it installs the proposal with a 128-bit CAS,
+// taking the key it has just read as the expected value (one dependent memory round trip
+// less per proposal), and a displaced suitor becomes the next proposer (the chain is
+// followed by the same tile).  Each lane takes up to two entries per round trip, issuing
+// the column, weight and key loads of both before comparing, so that a step costs four
+// dependent round trips (row pointers, row entries, keys, CAS) whatever the row length up
+// to 2T.  Every loop is capped; hitting a cap raises kErrTimeout and ends the tile.
 template <int T>
-__global__ void __launch_bounds__(256) k_suitor(int n, const int *__restrict__ rp,
-                                                const int *__restrict__ ci,
-                                                const double *__restrict__ w, SKey *S,
-                                                long long cap, int *err) {
+__global__ void __launch_bounds__(kSuitorBlock, 2048 / kSuitorBlock) k_suitor(int n, const int *__restrict__ rp,
+                                                                            const int *__restrict__ ci,
+                                                                            const double *__restrict__ w, SKey *S,
+                                                                            long long cap, int *err) {
   auto tile = cg::tiled_partition<T>(cg::this_thread_block());
   const int lane = tile.thread_rank();
-  const long long tile0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
-  const long long ntiles = (long long)gridDim.x * blockDim.x / T;
-  const long long per_tile = (n + ntiles - 1) / ntiles;
-  for (long long i = 0; i < per_tile; ++i) {
-    const long long u = CWM_SUITOR_ORDER == 1 ? tile0 * per_tile + i : tile0 + i * ntiles;
-    if (u >= n) break;
-    int current = (int)u;
-    long long steps = 0;
-    for (;;) {
-      if (++steps > cap) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        break;
-      }
-      const unsigned long long me = (unsigned long long)current + 1ull;
-      unsigned long long mc = 0ull;  // this lane's best candidate and the key it read there
-      int mx = -1;
-      SKey mk;
-      mk.lo = mk.hi = 0ull;
-      const int s = rp[current], e = rp[current + 1];
-      for (int k = s + lane; k < e; k += T) {
-        const double c = w[k];
-        if (!(c > 0.0)) continue;
-        const int x = ci[k];
-        const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
-        if (cb > mc || (cb == mc && x > mx)) {
-          const SKey cur = load_key(S + x);
-          if (gt(cb, me, cur.hi, cur.lo)) { mc = cb; mx = x; mk = cur; }
-        }
-      }
-      unsigned long long bc = mc;
-      int bx = mx;
-#pragma unroll
-      for (int o = T / 2; o > 0; o >>= 1) {
-        const unsigned long long oc = tile.shfl_xor(bc, o);
-        const int ox = tile.shfl_xor(bx, o);
-        if (oc > bc || (oc == bc && ox > bx)) { bc = oc; bx = ox; }
-      }
-      if (bx < 0) break;  // nobody would accept `current`: it stays unmatched
-      const int src = __ffs(tile.ballot(mx == bx)) - 1;  // the lane holding bx (>= 1 lane)
-      int next = -2;      // -2: beaten while proposing, rescan
-      if (lane == src) {
-        SKey mine;
-        mine.lo = me;
-        mine.hi = bc;
-        SKey expect = mk;
-        for (int t = 0; t < (1 << 22); ++t) {
-          if (!gt(bc, me, expect.hi, expect.lo)) break;
-          const SKey old = atomicCAS(S + bx, expect, mine);
-          if (old.lo == expect.lo && old.hi == expect.hi) {
-            next = (int)old.lo - 1;  // -1: x had no suitor
-            break;
-          }
-          expect = old;
-        }
-      }
-      next = tile.shfl(next, src);
-      if (next == -2) continue;
-      if (next < 0) break;
-      current = next;
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  if (t >= n) return;
+  int current = (int)(n - 1 - t);
+  long long steps = 0;
+  for (;;) {
+    if (++steps > cap) {
+      if (lane == 0) atomicOr(err, kErrTimeout);
+      break;
     }
+    const unsigned long long me = (unsigned long long)current + 1ull;
+    unsigned long long mc = 0ull;  // this lane's best candidate and the key it read there
+    int mx = -1;
+    SKey mk;
+    mk.lo = mk.hi = 0ull;
+    const int s = rp[current], e = rp[current + 1];
+    for (int k0 = s + lane; k0 < e; k0 += 2 * T) {
+      const int k1 = k0 + T;
+      const bool has1 = k1 < e;
+      const double c0 = w[k0];
+      const int x0 = ci[k0];
+      const double c1 = has1 ? w[k1] : 0.0;
+      const int x1 = has1 ? ci[k1] : 0;
+      const bool ok0 = c0 > 0.0, ok1 = c1 > 0.0;
+      SKey key0, key1;
+      key0.lo = key0.hi = key1.lo = key1.hi = 0ull;
+      if (ok0) key0 = load_key(S + x0);
+      if (ok1) key1 = load_key(S + x1);
+      const unsigned long long cb0 = (unsigned long long)__double_as_longlong(c0);
+      const unsigned long long cb1 = (unsigned long long)__double_as_longlong(c1);
+      if (ok0 && (cb0 > mc || (cb0 == mc && x0 > mx)) && gt(cb0, me, key0.hi, key0.lo)) {
+        mc = cb0; mx = x0; mk = key0;
+      }
+      if (ok1 && (cb1 > mc || (cb1 == mc && x1 > mx)) && gt(cb1, me, key1.hi, key1.lo)) {
+        mc = cb1; mx = x1; mk = key1;
+      }
+    }
+    unsigned long long bc = mc;
+    int bx = mx;
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) {
+      const unsigned long long oc = tile.shfl_xor(bc, o);
+      const int ox = tile.shfl_xor(bx, o);
+      if (oc > bc || (oc == bc && ox > bx)) { bc = oc; bx = ox; }
+    }
+    if (bx < 0) break;  // nobody would accept `current`: it stays unmatched
+    const int src = __ffs(tile.ballot(mx == bx)) - 1;  // the lane holding bx (>= 1 lane)
+    int next = -2;      // -2: beaten while proposing, rescan
+    if (lane == src) {
+      SKey mine;
+      mine.lo = me;
+      mine.hi = bc;
+      SKey expect = mk;
+      for (int q = 0; q < (1 << 22); ++q) {
+        if (!gt(bc, me, expect.hi, expect.lo)) break;
+        const SKey old = atomicCAS(S + bx, expect, mine);
+        if (old.lo == expect.lo && old.hi == expect.hi) {
+          next = (int)old.lo - 1;  // -1: x had no suitor
+          break;
+        }
+        expect = old;
+      }
+    }
+    next = tile.shfl(next, src);
+    if (next == -2) continue;
+    if (next < 0) break;
+    current = next;
   }
 }
 
@@ -390,8 +400,8 @@ amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, cons
   // Proposals are latency-bound: a tile of half the row length (two entries per lane)
   // keeps twice as many proposal chains in flight.
   const int T = tile_for_mean(mean / CWM_SUITOR_ENTRIES_PER_LANE);
-  const int block = 256;
-  const int grid = grid_for((long long)n * T, block, num_sms() * 8);
+  const int block = kSuitorBlock;
+  const unsigned grid = (unsigned)(((long long)n * T + block - 1) / block);
   switch (T) {
     case 4: k_suitor<4><<<grid, block, 0, s>>>(n, rp, ci, w, S, cap, d_err); break;
     case 8: k_suitor<8><<<grid, block, 0, s>>>(n, rp, ci, w, S, cap, d_err); break;
