@@ -202,6 +202,8 @@ amg_status cwm_aggregate(int n, const int32_t *d_mate, const double *d_v, int32_
  * (min(i,j), max(i,j), i) order; every hit (I,J) is stored, columns ascending.
  *   d_rpc (nc+1), d_colc and d_valc (capacity entries each) are device outputs;
  *   capacity >= nnz always suffices.  h_nnzc receives nnz(A_c).
+ *   Scratch (stream-ordered pool, freed on return): nnz ints and nnz doubles holding each
+ *   coarse row at a padded offset before the compaction into d_colc/d_valc.
  *   fp32 = 1: the binary32 variant (p_i, p_j, a_ij rounded to float, terms and sums in
  *   float in the same order, each entry stored as the double of its float); 0: float64.
  * Errors: INVALID_ARG (an aggregate with more than two members), UNSUPPORTED (a coarse

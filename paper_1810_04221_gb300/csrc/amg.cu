@@ -195,8 +195,9 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   const long long nnzf = F.nnz;
   DBuf<double> w, dv;
   DBuf<unsigned char> skeys;
-  DBuf<int> mate, m1, m2, ids, scan, cnt, longr, misc;
+  DBuf<int> mate, m1, m2, ids, scan, cnt, longr, misc, cpad;
   CWM_TRY(w.alloc(nnzf, s));
+  CWM_TRY(cpad.alloc(nnzf, s));
   CWM_TRY(dv.alloc(nf, s));
   CWM_TRY(skeys.alloc(suitor_scratch_bytes(nf), s));
   CWM_TRY(mate.alloc(nf, s));
@@ -247,15 +248,17 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
     CWM_TRY(o.diag.alloc(nc, s));
     GalerkinWork gw;
     gw.cnt = cnt.get();
+    gw.rpu = ids.get();  // the aggregation's scan output is free again
     gw.long_rows = longr.get();
     gw.n_long = misc.get() + 2;
     gw.scan = scan.get();
+    gw.ci_pad = cpad.get();
+    gw.val_pad = w.get();  // this sweep's weights are no longer needed
     gw.n_fine = cn;
     gw.nnz_fine = cnnz;
-    CWM_TRY(galerkin_count(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(), gw,
-                           h->err.get(), s));
-    CWM_TRY(galerkin_fill(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(),
-                          o.ci.get(), o.val.get(), o.diag.get(), nullptr, gw, fp32_galerkin, h->err.get(), s));
+    CWM_TRY(galerkin_group(crp, cci, cval, nc, m1.get(), m2.get(), o.agg.get(), o.p.get(), o.rp.get(),
+                           o.diag.get(), nullptr, gw, fp32_galerkin, h->err.get(), s));
+    CWM_TRY(galerkin_compact(nc, o.rp.get(), o.ci.get(), o.val.get(), gw, s));
     CWM_TRY(max_row_length(nc, o.rp.get(), misc.get() + 3, s));
     CWM_CUDA(cudaMemcpyAsync(h->box.ints + 4, o.rp.get() + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
     CWM_CUDA(cudaMemcpyAsync(h->box.ints + 5, misc.get() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1081,17 +1084,34 @@ amg_status cwm_galerkin(int n, const int32_t *d_row_ptr, const int32_t *d_col, c
   CWM_TRY(err.alloc(1, s));
   CWM_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
   CWM_TRY(members_from_agg(n, nc, d_agg, m1.get(), m2.get(), cnt.get(), err.get(), s));
+  int nnz_in = 0;  // nnz of the fine operator: the padded rows' capacity
+  if (n > 0) CWM_CUDA(cudaMemcpyAsync(&nnz_in, d_row_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, s));
   int h_err = 0;
-  CWM_TRY(read_bits(err.get(), &h_err, s, "cwm_galerkin (aggregates)"));
+  CWM_TRY(read_bits(err.get(), &h_err, s, "cwm_galerkin (aggregates)"));  // synchronises
+  if (nnz_in < 0) {
+    set_error("cwm_galerkin: row_ptr[n] = %d is negative", nnz_in);
+    return AMG_ERR_INVALID_ARG;
+  }
+  DBuf<int> rpu, cpad;
+  DBuf<double> vpad;
+  CWM_TRY(rpu.alloc((size_t)nc + 1, s));
+  CWM_TRY(cpad.alloc(nnz_in, s));
+  CWM_TRY(vpad.alloc(nnz_in, s));
   GalerkinWork gw;
   gw.cnt = cnt.get();
+  gw.rpu = rpu.get();
   gw.long_rows = longr.get();
   gw.n_long = misc.get();
   gw.scan = scan.get();
-  CWM_TRY(galerkin_count(d_row_ptr, d_col, d_val, nc, m1.get(), m2.get(), d_agg, d_p, d_rpc, gw, err.get(), s));
+  gw.ci_pad = cpad.get();
+  gw.val_pad = vpad.get();
+  gw.n_fine = n;
+  gw.nnz_fine = nnz_in;
+  CWM_TRY(galerkin_group(d_row_ptr, d_col, d_val, nc, m1.get(), m2.get(), d_agg, d_p, d_rpc, nullptr, nullptr, gw,
+                         fp32 != 0, err.get(), s));
   int nnzc = 0;
   CWM_CUDA(cudaMemcpyAsync(&nnzc, d_rpc + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CWM_TRY(read_bits(err.get(), &h_err, s, "cwm_galerkin (count)"));
+  CWM_TRY(read_bits(err.get(), &h_err, s, "cwm_galerkin (grouping)"));
   if (h_nnzc) *h_nnzc = nnzc;
   if (nnzc > capacity) {
     set_error("cwm_galerkin: nnz(A_c) = %d exceeds capacity %lld", nnzc, (long long)capacity);
@@ -1101,9 +1121,8 @@ amg_status cwm_galerkin(int n, const int32_t *d_row_ptr, const int32_t *d_col, c
     set_error("cwm_galerkin: NULL output arrays");
     return AMG_ERR_INVALID_ARG;
   }
-  CWM_TRY(galerkin_fill(d_row_ptr, d_col, d_val, nc, m1.get(), m2.get(), d_agg, d_p, d_rpc, d_colc, d_valc, nullptr,
-                        nullptr, gw, fp32 != 0, err.get(), s));
-  return read_bits(err.get(), &h_err, s, "cwm_galerkin (fill)");
+  CWM_TRY(galerkin_compact(nc, d_rpc, d_colc, d_valc, gw, s));
+  return read_bits(err.get(), &h_err, s, "cwm_galerkin (compaction)");
 }
 
 }  // extern "C"

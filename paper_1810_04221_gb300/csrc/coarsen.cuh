@@ -35,23 +35,25 @@ amg_status member_lists(int n, int nc, const int *agg, int *mptr, int *mlist, in
 
 // Galerkin product for a pairwise P (galerkin.cu).
 struct GalerkinWork {
-  int *cnt = nullptr;        // nc + 1 ints (row counts, then row pointers are written to rpc)
-  int *long_rows = nullptr;  // nc ints: coarse rows too long for the warp kernel
-  int *n_long = nullptr;     // 1 int
-  int *scan = nullptr;       // scan scratch
-  int n_fine = 0;            // fine size and nnz (for the tracer's byte counts)
+  int *cnt = nullptr;         // nc + 1 ints: padded lengths, then distinct-column counts
+  int *rpu = nullptr;         // nc + 1 ints: padded row starts
+  int *long_rows = nullptr;   // nc ints: coarse rows too long for the warp kernel
+  int *n_long = nullptr;      // 1 int
+  int *scan = nullptr;        // scan scratch
+  int *ci_pad = nullptr;      // nnz_fine ints: padded columns
+  double *val_pad = nullptr;  // nnz_fine doubles: padded values
+  int n_fine = 0;             // fine size and nnz
   long long nnz_fine = 0;
 };
-// Pass 1: row counts of A_c, scanned into rpc (rpc[nc] = nnz(A_c) on the device).
-amg_status galerkin_count(const int *rp, const int *ci, const double *val, int nc, const int *m1,
-                          const int *m2, const int *agg, const double *p, int *rpc,
-                          const GalerkinWork &work, int *d_err, cudaStream_t s);
-// Pass 2: columns and values of A_c at rpc; diag_c (nc) and dl1_c (nc) may be NULL.
-// fp32: terms and sums in binary32 (values stored as doubles of floats).
-amg_status galerkin_fill(const int *rp, const int *ci, const double *val, int nc, const int *m1,
-                         const int *m2, const int *agg, const double *p, const int *rpc, int *cic,
-                         double *valc, double *diag_c, double *dl1_c, const GalerkinWork &work,
-                         bool fp32, int *d_err, cudaStream_t s);
+// Groups the entries of every coarse row into the padded arrays and writes the row
+// pointers of A_c to rpc (rpc[nc] = nnz(A_c) on the device); diag_c (nc) and dl1_c (nc)
+// may be NULL.  fp32: terms and sums in binary32 (values stored as doubles of floats).
+amg_status galerkin_group(const int *rp, const int *ci, const double *val, int nc, const int *m1,
+                          const int *m2, const int *agg, const double *p, int *rpc, double *diag_c,
+                          double *dl1_c, const GalerkinWork &work, bool fp32, int *d_err, cudaStream_t s);
+// Copies the padded rows to cic/valc at rpc (capacity rpc[nc]).
+amg_status galerkin_compact(int nc, const int *rpc, int *cic, double *valc, const GalerkinWork &work,
+                            cudaStream_t s);
 // m1/m2 from agg when the caller only has agg (cwm_galerkin): members in ascending order;
 // an empty aggregate or one with more than two members raises kErrInvalid.  cnt: nc ints.
 amg_status members_from_agg(int n, int nc, const int *agg, int *m1, int *m2, int *cnt, int *d_err,

@@ -1,5 +1,10 @@
 // galerkin.cu -- Galerkin product A_c = P^T A P (Sec. 2.1; the costliest setup step per
-// Sec. 3.1) for the pairwise P of one matching sweep, in two passes (count, fill).
+// Sec. 3.1) for the pairwise P of one matching sweep, in one grouping pass: each coarse row
+// is written at a padded offset (the sum of its member rows' lengths, an upper bound on its
+// length) together with its number of distinct columns; a scan of those counts gives the
+// row pointers, and a compaction copies the rows into place.  (A separate counting pass
+// repeated the whole grouping -- the sorts of long rows included -- only to size the
+// output.)
 //
 // Coarse row I has members i1 < i2 (or i1 alone).  The fine entries of rows i1 and i2 are
 // keyed by (J = agg(j), local slot) and sorted in shared memory (bitonic), so equal J are
@@ -158,10 +163,8 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
   const unsigned mm = __match_any_sync(gmask, J);
   const bool leader = act && lane == __ffs(mm) - 1;
   const unsigned lead = __ballot_sync(gmask, leader) & gmask;
-  if (!FILL) {
-    if (gl == 0) cnt[I] = __popc(lead);
-    return;
-  }
+  if (gl == 0 && cnt) cnt[I] = __popc(lead);
+  if (!FILL) return;
   Acc t = Acc(0);
   int kmin = 0, kmax = 0;
   if (act) {
@@ -273,7 +276,7 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
     }
     base += __popc(ball);
   }
-  if (!FILL && lane == 0) cnt[I] = base;
+  if (cnt && lane == 0) cnt[I] = base;
   __syncwarp();
 }
 
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         galerkin_row_reg<FILL, Acc>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (L <= kWarpCap) {
         galerkin_row_smem<FILL, Acc>(r, I, keys, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
-      } else if (!FILL && lane == 0) {
+      } else if (long_rows && lane == 0) {
         long_rows[atomicAdd(n_long, 1)] = I;
       }
       __syncwarp();
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(kLongThreads)
     if (L > kBlockCap) {
       if (tid == 0) {
         atomicOr(err, kErrUnsupported);
-        if (!FILL) cnt[I] = 0;
+        if (cnt) cnt[I] = 0;
       }
       continue;
     }
@@ -402,9 +405,8 @@ __global__ void __launch_bounds__(kLongThreads)
       base += chunk;
       __syncthreads();
     }
-    if (!FILL) {
-      if (tid == 0) cnt[I] = base;
-    } else if (dl1_c) {
+    if (cnt && tid == 0) cnt[I] = base;
+    if (FILL && dl1_c) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
       if (lane == 0) wl1[warp] = l1;
@@ -436,54 +438,76 @@ static amg_status galerkin_attrs() {
   return AMG_OK;
 }
 
-amg_status galerkin_count(const int *rp, const int *ci, const double *val, int nc, const int *m1,
-                          const int *m2, const int *agg, const double *p, int *rpc,
-                          const GalerkinWork &work, int *d_err, cudaStream_t s) {
+// cnt[I] = L1 + L2: the number of fine entries that coarse row I gathers, an upper bound
+// on its length (its padded row length).
+__global__ void k_gather_lengths(int nc, const int *__restrict__ rp, const int *__restrict__ m1,
+                                 const int *__restrict__ m2, int *__restrict__ cnt) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  const int i1 = m1[I], i2 = m2[I];
+  cnt[I] = rp[i1 + 1] - rp[i1] + (i2 >= 0 ? rp[i2 + 1] - rp[i2] : 0);
+}
+
+// Copies row I from its padded place [rpu[I], rpu[I] + len) to [rpc[I], rpc[I+1]); an
+// 8-lane tile per row.
+__global__ void k_galerkin_compact(int nc, const int *__restrict__ rpu, const int *__restrict__ rpc,
+                                   const int *__restrict__ ci_pad, const double *__restrict__ val_pad,
+                                   int *__restrict__ cic, double *__restrict__ valc) {
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int lane = threadIdx.x & 7;
+  const long long nt = ((long long)gridDim.x * blockDim.x) >> 3;
+  for (long long I = t; I < nc; I += nt) {
+    const int src = rpu[I], dst = rpc[I], len = rpc[I + 1] - dst;
+    for (int q = lane; q < len; q += 8) {
+      cic[dst + q] = ci_pad[src + q];
+      valc[dst + q] = val_pad[src + q];
+    }
+  }
+}
+
+amg_status galerkin_group(const int *rp, const int *ci, const double *val, int nc, const int *m1,
+                          const int *m2, const int *agg, const double *p, int *rpc, double *diag_c,
+                          double *dl1_c, const GalerkinWork &work, bool fp32, int *d_err, cudaStream_t s) {
   if (nc == 0) {
     CWM_CUDA(cudaMemsetAsync(rpc, 0, sizeof(int), s));
     return AMG_OK;
   }
   CWM_TRY(galerkin_attrs());
-  // members and row bounds, ci and agg(ci) of both member rows, counts, scan
-  CWM_TRACE("galerkin_count", 4.0 * work.nnz_fine + 4.0 * work.n_fine + 40.0 * nc, s);
+  // members and row bounds, ci, agg(ci), val and p of both member rows; the padded rows
+  // written (columns and values), the counts and both scans
+  CWM_TRACE("galerkin", 16.0 * work.nnz_fine + 16.0 * work.n_fine + 72.0 * nc + 12.0 * work.nnz_fine, s);
+  k_gather_lengths<<<grid_for(nc, 256, 1 << 30), 256, 0, s>>>(nc, rp, m1, m2, work.cnt);
+  CWM_LAUNCH();
+  CWM_TRY(exclusive_scan(work.cnt, work.rpu, nc, work.scan, s));
   const int block = kWarpsPerBlock * 32;
   const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
   CWM_CUDA(cudaMemsetAsync(work.n_long, 0, sizeof(int), s));
-  k_galerkin_warp<false, double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, nullptr,
-                                                nullptr, nullptr, nullptr, work.long_rows, work.n_long, d_err);
-  CWM_LAUNCH();
-  k_galerkin_block<false, double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
-      rp, ci, val, m1, m2, agg, p, work.cnt, nullptr, nullptr, nullptr, nullptr, nullptr,
-      work.long_rows, work.n_long, d_err);
+  if (fp32) {
+    k_galerkin_warp<true, float><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
+                                                        work.ci_pad, work.val_pad, diag_c, work.long_rows,
+                                                        work.n_long, d_err);
+    CWM_LAUNCH();
+    k_galerkin_block<true, float><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+        rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu, work.ci_pad, work.val_pad, diag_c, dl1_c,
+        work.long_rows, work.n_long, d_err);
+  } else {
+    k_galerkin_warp<true, double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
+                                                         work.ci_pad, work.val_pad, diag_c, work.long_rows,
+                                                         work.n_long, d_err);
+    CWM_LAUNCH();
+    k_galerkin_block<true, double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+        rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu, work.ci_pad, work.val_pad, diag_c, dl1_c,
+        work.long_rows, work.n_long, d_err);
+  }
   CWM_LAUNCH();
   return exclusive_scan(work.cnt, rpc, nc, work.scan, s);
 }
 
-amg_status galerkin_fill(const int *rp, const int *ci, const double *val, int nc, const int *m1,
-                         const int *m2, const int *agg, const double *p, const int *rpc, int *cic,
-                         double *valc, double *diag_c, double *dl1_c, const GalerkinWork &work,
-                         bool fp32, int *d_err, cudaStream_t s) {
+amg_status galerkin_compact(int nc, const int *rpc, int *cic, double *valc, const GalerkinWork &work,
+                            cudaStream_t s) {
   if (nc == 0) return AMG_OK;
-  CWM_TRY(galerkin_attrs());
-  // reads as in the count pass plus val and p; writes of A_c not included (size unknown here)
-  CWM_TRACE("galerkin_fill", 12.0 * work.nnz_fine + 12.0 * work.n_fine + 44.0 * nc, s);
-  const int block = kWarpsPerBlock * 32;
-  const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
-  if (fp32) {
-    k_galerkin_warp<true, float><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic,
-                                                        valc, diag_c, nullptr, nullptr, d_err);
-    CWM_LAUNCH();
-    k_galerkin_block<true, float><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
-        rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic, valc, diag_c, dl1_c, work.long_rows,
-        work.n_long, d_err);
-  } else {
-    k_galerkin_warp<true, double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic,
-                                                         valc, diag_c, nullptr, nullptr, d_err);
-    CWM_LAUNCH();
-    k_galerkin_block<true, double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
-        rp, ci, val, m1, m2, agg, p, nullptr, rpc, cic, valc, diag_c, dl1_c, work.long_rows,
-        work.n_long, d_err);
-  }
+  k_galerkin_compact<<<grid_for((long long)nc * 8, 256, num_sms() * 8), 256, 0, s>>>(
+      nc, work.rpu, rpc, work.ci_pad, work.val_pad, cic, valc);
   CWM_LAUNCH();
   return AMG_OK;
 }
