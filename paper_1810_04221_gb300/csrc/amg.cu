@@ -40,18 +40,32 @@ struct Level {
   DBuf<double> xdense;
   DBuf<float> xdense32;
 
+  // rows longer than long_min, taken by a whole warp in the l1-Jacobi sweep (n_long = 0: none)
+  DBuf<int> long_rows;
+  int n_long = 0, long_min = 0;
+
+  template <class V>
+  void split(CsrView<V> &a, bool fp64) const {
+    a.max_row = max_row;
+    if (a.rb || n_long <= 0) return;
+    bool rb_unused = false;
+    a.long_rows = long_rows.get();
+    a.n_long = n_long;
+    a.long_min = long_min;
+    row_kernel_shape(n, nnz, long_min, fp64, &rb_unused, &a.tile_short);
+  }
   CsrView<double> view64() const {
     CsrView<double> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val.get();
     row_kernel_shape(n, nnz, max_row, true, &a.rb, &a.tile);
-    a.max_row = max_row;
+    split(a, true);
     return a;
   }
   CsrView<float> view32() const {
     CsrView<float> a;
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get();
     row_kernel_shape(n, nnz, max_row, false, &a.rb, &a.tile);
-    a.max_row = max_row;
+    split(a, false);
     return a;
   }
 };
@@ -313,6 +327,28 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
 
 amg_status finish_level(amg_hierarchy *h, Level &L) {
   cudaStream_t s = h->stream;
+  {  // the long rows of a sub-warp-tile level (see long_row_min)
+    bool rb64 = true, rb32 = true;
+    int t = 0;
+    row_kernel_shape(L.n, L.nnz, L.max_row, true, &rb64, &t);
+    row_kernel_shape(L.n, L.nnz, L.max_row, false, &rb32, &t);
+    const int lim = long_row_min(L.n, L.nnz, L.max_row, rb64, rb32);
+    if (lim > 0) {
+      int *cnt = h->err.get() + 1;  // scratch word next to the error bits
+      CWM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+      CWM_TRY(long_row_list(L.n, L.rp.get(), lim, nullptr, cnt, s));
+      CWM_CUDA(cudaMemcpyAsync(h->box.ints + 6, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CWM_TRY(read_err(h, "amg_setup (long rows)"));
+      const int nlong = h->box.ints[6];
+      if (nlong > 0) {
+        CWM_TRY(L.long_rows.alloc(nlong, s));
+        CWM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+        CWM_TRY(long_row_list(L.n, L.rp.get(), lim, L.long_rows.get(), cnt, s));
+        L.n_long = nlong;
+        L.long_min = lim;
+      }
+    }
+  }
   CWM_TRY(L.dinv.alloc(L.n, s));
   const bool f32 = h->prm.vcycle_fp32 != 0;
   if (f32) CWM_TRY(L.dinv32.alloc(L.n, s));

@@ -2,6 +2,8 @@
 // per row, the l1-Jacobi sweep (Sec. 3.2), residual + restriction by the aggregation
 // prolongator, prolongation, the one-block coarsest solve, and the fused FCG kernels of
 // Sec. 3.2 (three dot products in one pass with the SpMV, paired vector updates).
+#include <algorithm>
+
 #include "solve.cuh"
 
 namespace cwm {
@@ -237,6 +239,40 @@ __global__ void k_max_row(int n, const int *__restrict__ rp, int *out) {
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 
+#ifndef CWM_LONG_ROW_MIN
+#define CWM_LONG_ROW_MIN 64
+#endif
+#ifndef CWM_LONG_ROW_FACTOR
+#define CWM_LONG_ROW_FACTOR 8
+#endif
+// A row is long when it is longer than CWM_LONG_ROW_MIN entries and CWM_LONG_ROW_FACTOR
+// times the mean: a few hub rows (a lognormal coarse level: mean 5, longest 176) then no
+// longer set the tile width and the time of every sweep, while levels whose rows are all
+// long (Q1 elasticity: mean 64) keep their shape.  Only levels on sub-warp tiles in some
+// precision (rb64 or rb32 false) split.
+int long_row_min(int n, long long nnz, int max_row, bool rb64, bool rb32) {
+  if (n <= 0 || (rb64 && rb32)) return 0;
+  const double mean = (double)nnz / n;
+  const double lim = std::max((double)CWM_LONG_ROW_MIN, CWM_LONG_ROW_FACTOR * mean);
+  return max_row > lim ? (int)lim : 0;
+}
+
+__global__ void k_long_rows(int n, const int *__restrict__ rp, int min_len, int *list, int *count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (rp[i + 1] - rp[i] > min_len) {
+      const int q = atomicAdd(count, 1);
+      if (list) list[q] = (int)i;
+    }
+  }
+}
+
+amg_status long_row_list(int n, const int *rp, int min_len, int *list, int *d_count, cudaStream_t s) {
+  if (n <= 0) return AMG_OK;
+  k_long_rows<<<grid_for(n, kBlock, num_sms() * 4), kBlock, 0, s>>>(n, rp, min_len, list, d_count);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
 amg_status max_row_length(int n, const int *rp, int *d_out, cudaStream_t s) {
   CWM_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int), s));
   if (n <= 0) return AMG_OK;
@@ -322,6 +358,37 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
   }
 }
 
+// The split sweep: blocks [0, long_blocks) give each listed long row a whole warp; the
+// other blocks run the tile loop over all rows and skip the long ones (length > long_min).
+template <class V, int T>
+__global__ void __launch_bounds__(kBlock)
+    k_jacobi_split(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ val,
+                   const V *__restrict__ dinv, const V *__restrict__ b, const V *__restrict__ x, V *__restrict__ y,
+                   const int *__restrict__ long_rows, int n_long, int long_min, int long_blocks) {
+  pdl_begin();
+  if ((int)blockIdx.x < long_blocks) {
+    const int lane = threadIdx.x & 31;
+    const int nw = long_blocks * (kBlock / 32);
+    for (int q = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); q < n_long; q += nw) {
+      const int row = long_rows[q];
+      const V dot = tile_row_dot<V, 32>(rp, ci, val, x, row, true, lane);
+      if (lane == 0) y[row] = x[row] + dinv[row] * (b[row] - dot);
+    }
+    return;
+  }
+  const int lane = threadIdx.x & (T - 1);
+  const int sub = (threadIdx.x & 31) / T;
+  constexpr int kRowsPerWarp = 32 / T;
+  const long long warp_id = ((long long)(blockIdx.x - long_blocks) * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)(gridDim.x - long_blocks) * blockDim.x) >> 5;
+  for (long long base = warp_id * kRowsPerWarp; base < n; base += nwarps * kRowsPerWarp) {
+    const long long row = base + sub;
+    const bool active = row < n && rp[row + 1] - rp[row] <= long_min;
+    const V dot = tile_row_dot<V, T>(rp, ci, val, x, row, active, lane);
+    if (active && lane == 0) y[row] = x[row] + dinv[row] * (b[row] - dot);
+  }
+}
+
 template <class V>
 __global__ void __launch_bounds__(kRB) k_jacobi_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                    const V *__restrict__ val, const V *__restrict__ dinv,
@@ -343,6 +410,10 @@ amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V 
   CWM_TRACE("jacobi", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 4.0 * sizeof(V) * A.n, s);
   if (A.rb) {
     CWM_CUDA(launch_pdl(k_jacobi_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, x, y));
+  } else if (A.n_long > 0) {
+    const int lb = (int)std::min<long long>((A.n_long + kBlock / 32 - 1) / (kBlock / 32), (long long)num_sms() * 2);
+    CWM_DISPATCH_T(A.tile_short, CWM_CUDA(launch_pdl(k_jacobi_split<V, kT>, rows_grid(A.n, kT) + lb, kBlock, 0, s, A.n, A.rp, A.ci,
+                                               A.val, dinv, b, x, y, A.long_rows, A.n_long, A.long_min, lb)));
   } else {
     CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_jacobi<V, kT>, rows_grid(A.n, kT), kBlock, 0, s, A.n, A.rp, A.ci, A.val, dinv, b,
                                                                                 x, y)));

@@ -17,6 +17,13 @@ struct CsrView {
   int tile = 8;  // sub-warp width chosen from the row lengths (tile_for_rows)
   bool rb = true;  // row-block kernels (else a sub-warp tile per row): row_kernel_shape()
   int max_row = 0;  // longest row (0: unknown)
+  // Rows longer than long_min (listed in long_rows[0 .. n_long)) are taken by a whole warp
+  // in the l1-Jacobi sweep of a sub-warp-tile level; the tile width then follows the
+  // remaining rows.  n_long = 0: no split.
+  const int *long_rows = nullptr;
+  int n_long = 0;
+  int long_min = 0;
+  int tile_short = 8;  // tile width of the split sweep's other rows
 };
 
 // Shape of a level's solve kernels: row blocks (a thread per row, CSR chunks staged in
@@ -30,6 +37,12 @@ struct CsrView {
 void row_kernel_shape(int n, long long nnz, int max_row, bool fp64, bool *rb, int *tile);
 // *d_out = the longest row of the CSR pattern rp (device int; asynchronous)
 amg_status max_row_length(int n, const int *rp, int *d_out, cudaStream_t s);
+// Length above which a row of a sub-warp-tile level is a "long row" for the split sweep
+// (0: the level keeps one tile width for all rows).
+int long_row_min(int n, long long nnz, int max_row, bool rb64, bool rb32);
+// *d_count = number of rows longer than min_len; with list != NULL they are also written
+// to list (in no particular order).  d_count must be zeroed by the caller.
+amg_status long_row_list(int n, const int *rp, int min_len, int *list, int *d_count, cudaStream_t s);
 
 // Largest coarsest level solved by the one-block kernel (x kept in shared memory).
 constexpr int kCoarseBlockMax = 2048;

@@ -206,6 +206,28 @@ def random_spd(n: int, avg_degree: float = 4.0, seed: int = 0, ties: bool = Fals
                       np.concatenate([w, w, diag]))
 
 
+def random_spd_hubs(n: int, avg_degree: float = 4.0, n_hubs: int = 8, hub_degree: int = 300, seed: int = 0):
+    """random_spd plus n_hubs vertices joined to hub_degree random others each: a few rows
+    far longer than the mean, like the hub rows of a lognormal coarse level."""
+    rng = np.random.default_rng(seed)
+    m = int(avg_degree * n / 2)
+    a = rng.integers(0, n, size=m)
+    b = rng.integers(0, n, size=m)
+    hubs = rng.choice(n, size=n_hubs, replace=False)
+    a = np.concatenate([a, np.repeat(hubs, hub_degree)])
+    b = np.concatenate([b, rng.integers(0, n, size=n_hubs * hub_degree)])
+    keep = a != b
+    a, b = np.minimum(a[keep], b[keep]), np.maximum(a[keep], b[keep])
+    pairs = np.unique(a.astype(np.int64) * n + b)
+    a, b = pairs // n, pairs % n
+    w = -rng.uniform(0.1, 1.0, size=len(a))
+    rowsum = np.bincount(a, weights=np.abs(w), minlength=n) + np.bincount(b, weights=np.abs(w), minlength=n)
+    diag = rowsum + rng.uniform(0.1, 1.0, size=n)
+    d = np.arange(n, dtype=np.int64)
+    return _exact_csr(n, np.concatenate([a, b, d]), np.concatenate([b, a, d]),
+                      np.concatenate([w, w, diag]))
+
+
 def smooth_vector_ones(n: int) -> np.ndarray:
     return np.ones(n, np.float64)
 

@@ -74,6 +74,34 @@ def test_coarsest_above_dense_limit():
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def _long_rows(mat):
+    """Rows the split l1-Jacobi sweep gives a whole warp: longer than max(64, 8 x mean)."""
+    rp = mat[0]
+    n = len(rp) - 1
+    lens = np.diff(rp)
+    return int((lens > max(64.0, 8.0 * len(mat[1]) / n)).sum())
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_long_row_split_coarsest(fp32):
+    """A single-level hierarchy (the coarsest level above the dense limit) whose hub rows
+    take the split sweep: 20 l1-Jacobi sweeps, each hub row on a whole warp."""
+    mat = P.random_spd_hubs(5000, 4.0, n_hubs=12, hub_degree=300, seed=7)
+    assert _long_rows(mat) >= 12
+    got, ref = _vcycle_pair(mat, 2, 10_000, dict(tail_rows=-1, vcycle_fp32=fp32))
+    tol = 2e-5 if fp32 else 1e-12
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_long_row_split_hierarchy(fp32):
+    """Hub rows on every level of a multi-level hierarchy (post-smoothing sweeps split too)."""
+    mat = P.random_spd_hubs(20000, 4.0, n_hubs=40, hub_degree=400, seed=8)
+    got, ref = _vcycle_pair(mat, 2, 60, dict(tail_rows=-1, vcycle_fp32=fp32))
+    tol = 2e-5 if fp32 else 1e-12
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("tail_rows", [-1, 0])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_vcycle_fp32(case, tail_rows):
