@@ -78,45 +78,11 @@ amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, 
 }
 
 // ------------------------------------------------------------ edge weights ----
-// Sec. 2.2, C(A, v): one T-lane tile per row; lanes stride over the row's slots.
-// No FMA: every product and sum is an explicit round-to-nearest intrinsic in the
-// order ((2 a) v_a) v_b over ((a_aa v_a) v_a) + ((a_bb v_b) v_b), a = min(i,j).
-template <int T>
-__global__ void __launch_bounds__(256) k_edge_weights(int n, const int *__restrict__ rp,
-                                                      const int *__restrict__ ci,
-                                                      const double *__restrict__ val,
-                                                      const double *__restrict__ diag,
-                                                      const double *__restrict__ v,
-                                                      double *__restrict__ w) {
-  const int lane = threadIdx.x & (T - 1);
-  const long long tile0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
-  const long long ntiles = (long long)gridDim.x * blockDim.x / T;
-  for (long long row = tile0; row < n; row += ntiles) {
-    const int i = (int)row;
-    const int s = rp[i], e = rp[i + 1];
-    const double vi = v[i], di = diag[i];
-    for (int k = s + lane; k < e; k += T) {
-      const int j = ci[k];
-      const double a = val[k];
-      double c = 0.0;
-      if (j != i && a != 0.0) {
-        const double vj = __ldg(v + j), dj = __ldg(diag + j);
-        const bool lo_i = i < j;
-        const double va = lo_i ? vi : vj, vb = lo_i ? vj : vi;
-        const double da = lo_i ? di : dj, db = lo_i ? dj : di;
-        const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), va), vb);
-        const double den = __dadd_rn(__dmul_rn(__dmul_rn(da, va), va), __dmul_rn(__dmul_rn(db, vb), vb));
-        if (den != 0.0) {
-          const double cc = __dsub_rn(1.0, __ddiv_rn(num, den));
-          if (cc > 0.0) c = cc;
-        }
-      }
-      w[k] = c;
-    }
-  }
-}
-
-// Row-block form of the same computation, evaluating each edge once.  A block of kWB
+// Sec. 2.2, C(A, v).  No FMA: every product and sum is an explicit round-to-nearest
+// intrinsic in the order ((2 a) v_a) v_b over ((a_aa v_a) v_a) + ((a_bb v_b) v_b),
+// a = min(i,j).
+//
+// Row blocks, evaluating each edge once.  A block of kWB
 // threads owns kWB consecutive rows.  Each row's thread finds where its upper part
 // (columns > i) starts, writes 0 into its diagonal slot, and the block packs the upper
 // slots of all its rows into one dense list (an exclusive scan of the per-row counts);
@@ -201,13 +167,13 @@ __global__ void __launch_bounds__(kWB) k_edge_weights_rb(int n, const int *__res
       const int il = s_row[c0 + e * kWB + t - c0];
       const int i = r0 + il, j = col[e];  // i < j: row i is the smaller index
       double c = 0.0;
-      if (a[e] != 0.0) {
+      if (nonzero_f64(a[e])) {
         const double va = s_v[il], vb = __ldg(v + j);
         const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a[e]), va), vb);
         const double den = __dadd_rn(s_d[il], __ldg(dv + j));
-        if (den != 0.0) {
+        if (nonzero_f64(den)) {
           const double cc = __dsub_rn(1.0, __ddiv_rn(num, den));
-          if (cc > 0.0) c = cc;
+          if (pos_f64(cc)) c = cc;
         }
       }
       __stcs(w + slot[e], c);
@@ -331,7 +297,7 @@ __global__ void __launch_bounds__(kSuitorBlock, 2048 / kSuitorBlock) k_suitor(in
       const int x0 = ci[k0];
       const double c1 = has1 ? w[k1] : 0.0;
       const int x1 = has1 ? ci[k1] : 0;
-      const bool ok0 = c0 > 0.0, ok1 = c1 > 0.0;
+      const bool ok0 = pos_f64(c0), ok1 = pos_f64(c1);
       SKey key0, key1;
       key0.lo = key0.hi = key1.lo = key1.hi = 0ull;
       if (ok0) key0 = load_key(S + x0);

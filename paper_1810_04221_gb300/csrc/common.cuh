@@ -167,6 +167,19 @@ inline int grid_for(long long items, int per_block, int cap_blocks) {
   return (int)b;
 }
 // Sub-warp ("miniwarp") width for rows of `mean` stored entries: 4, 8, 16 or 32.
+// FP64 comparisons against zero on the integer pipes.  GB300 retires FP64 instructions --
+// compares included -- at a small fraction of its other rates, so a compare inside a
+// latency-bound loop waits for that pipe; these give the IEEE results exactly.
+//   pos_f64(x)     == (x > 0.0): positive sign bit clear, not +0.0, not NaN (+inf counts)
+//   nonzero_f64(x) == (x != 0.0): any bits other than the sign bit (NaN counts)
+__device__ __forceinline__ bool pos_f64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0ll && b <= 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool nonzero_f64(double x) {
+  return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+}
+
 inline int tile_for_mean(double mean) {
   if (mean <= 4.5) return 4;
   if (mean <= 9.0) return 8;
