@@ -450,8 +450,16 @@ void fill_tail(amg_hierarchy *h, int k0, TailArgs<V> &a) {
 template <class V>
 amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init);
 
-// Largest level whose cycle uses the fused kernels (see cycle_level).
-constexpr int kFuseMaxRows = 300000;
+// Largest level whose cycle uses the fused kernels (see cycle_level), per precision.  The
+// fused forms rebuild x_j per nonzero (D^{-1} b, and D^{-1} b + P x_c), two or three FP64
+// operations per nonzero instead of one; where GB300's FP64 pipe binds, that costs more
+// than the passes saved.  3D Poisson 128^3, FP64 V-cycle: limits of 300000 / 65536 / 0 rows
+// gave 11.61 / 11.41 / 11.62 ms per solve (level 1 has 262,144 rows).
+#ifndef CWM_FUSE_MAX_ROWS64
+#define CWM_FUSE_MAX_ROWS64 65536
+#endif
+template <class V>
+constexpr int fuse_max_rows() { return sizeof(V) == 8 ? CWM_FUSE_MAX_ROWS64 : 300000; }
 
 // x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
 template <class V>
@@ -512,7 +520,7 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   // inside the post-sweep, two kernels fewer.  On large levels the extra gathers per
   // nonzero cost more than the passes they save (measured), so they keep separate kernels;
   // so do levels on sub-warp tiles (the fused forms exist as row-block kernels only).
-  if (zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= kFuseMaxRows && A.rb) {
+  if (zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= fuse_max_rows<V>() && A.rb) {
     CWM_TRY(resid_scaled_restrict<V>(A, C0.n, L.mptr.get(), L.mlist.get(), LV::p(L), dinv, b, t1, LV::b(C0), s));
     for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C0), LV::x(C0), g == 0));
     return prolong_jacobi<V>(A, dinv, b, L.agg.get(), LV::p(L), LV::x(C0), x, s);
