@@ -157,13 +157,16 @@ __device__ __forceinline__ V rb_row_dot_x(const int *__restrict__ ci, const V *_
 }
 
 // Row dot of row r0 + threadIdx.x with x (0 for threads beyond nrows); ABS = sum of |a_ij|.
-template <class V, bool ABS>
+// NEG: init - sum_j a_ij x_j, the products subtracted from init by the FMA chain itself
+// (the residual b_i - (A x)_i without a separate FP64 subtraction).
+template <class V, bool ABS, bool NEG = false>
 __device__ __forceinline__ V rb_row_dot(const int *__restrict__ ci, const V *__restrict__ val,
-                                        const V *__restrict__ x, int nrows, RowBlockSmem<V> &sm) {
+                                        const V *__restrict__ x, int nrows, RowBlockSmem<V> &sm,
+                                        V init = V(0)) {
   const int t = threadIdx.x;
   const int rs = sm.rp[0], re = sm.rp[nrows];
   const int my_s = t < nrows ? sm.rp[t] : 0, my_e = t < nrows ? sm.rp[t + 1] : 0;
-  V acc = V(0);
+  V acc = init;
   for (int c0 = rs; c0 < re; c0 += kRBC) {
     const int cend = min(c0 + kRBC, re);
     int col[kRBE];
@@ -187,15 +190,16 @@ __device__ __forceinline__ V rb_row_dot(const int *__restrict__ ci, const V *__r
       for (; k < hi; ++k) acc += fabs(sm.val[k]);
     } else {
       // four independent gathers in flight, then the FMAs in order
+      const V sg = NEG ? V(-1) : V(1);
       for (; k + 4 <= hi; k += 4) {
         const V x0 = __ldg(x + sm.col[k]), x1 = __ldg(x + sm.col[k + 1]);
         const V x2 = __ldg(x + sm.col[k + 2]), x3 = __ldg(x + sm.col[k + 3]);
-        acc = fma(sm.val[k], x0, acc);
-        acc = fma(sm.val[k + 1], x1, acc);
-        acc = fma(sm.val[k + 2], x2, acc);
-        acc = fma(sm.val[k + 3], x3, acc);
+        acc = fma(sg * sm.val[k], x0, acc);
+        acc = fma(sg * sm.val[k + 1], x1, acc);
+        acc = fma(sg * sm.val[k + 2], x2, acc);
+        acc = fma(sg * sm.val[k + 3], x3, acc);
       }
-      for (; k < hi; ++k) acc = fma(sm.val[k], __ldg(x + sm.col[k]), acc);
+      for (; k < hi; ++k) acc = fma(sg * sm.val[k], __ldg(x + sm.col[k]), acc);
     }
     __syncthreads();
   }
@@ -399,9 +403,9 @@ __global__ void __launch_bounds__(kRB) k_jacobi_rb(int n, const int *__restrict_
   const int r0 = blockIdx.x * kRB;
   const int nrows = min(kRB, n - r0);
   rb_stage_rp(rp, r0, nrows, sm.rp);
-  const V dot = rb_row_dot<V, false>(ci, val, x, nrows, sm);
   const int r = r0 + threadIdx.x;
-  if (threadIdx.x < nrows) y[r] = x[r] + dinv[r] * (b[r] - dot);
+  const V res = rb_row_dot<V, false, true>(ci, val, x, nrows, sm, threadIdx.x < nrows ? b[r] : V(0));
+  if (threadIdx.x < nrows) y[r] = fma(dinv[r], res, x[r]);
 }
 
 template <class V>
@@ -548,9 +552,10 @@ __global__ void __launch_bounds__(kRB) k_resid_rb(int n, const int *__restrict__
   const int r0 = blockIdx.x * kRB;
   const int nrows = min(kRB, n - r0);
   rb_stage_rp(rp, r0, nrows, sm.rp);
-  const V dot = x ? rb_row_dot<V, false>(ci, val, x, nrows, sm) : V(0);
   const int i = r0 + threadIdx.x;
-  if (threadIdx.x < nrows) r[i] = b[i] - dot;
+  const V bi = threadIdx.x < nrows ? b[i] : V(0);
+  const V res = x ? rb_row_dot<V, false, true>(ci, val, x, nrows, sm, bi) : bi;
+  if (threadIdx.x < nrows) r[i] = res;
 }
 
 // r = b - A x (x may be NULL: r = b), a sub-warp tile per row
