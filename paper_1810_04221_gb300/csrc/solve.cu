@@ -12,11 +12,14 @@ constexpr int kBlock = 256;
 
 // All T lanes of every tile of the warp call this together (warp-uniform loops), so the
 // full-mask shuffles are well defined; inactive tiles contribute zero.
-template <class V, int T>
+// NEG: returns init - sum_j a_ij x_j, lane 0 starting from init and every lane subtracting
+// its products (no separate FP64 subtraction).
+template <class V, int T, bool NEG = false>
 __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int *__restrict__ ci,
                                           const V *__restrict__ val, const V *__restrict__ x, long long row,
-                                          bool active, int lane) {
-  V s = V(0);
+                                          bool active, int lane, V init = V(0)) {
+  V s = (NEG && lane == 0) ? init : V(0);
+  const V sg = NEG ? V(-1) : V(1);
   if (active && x) {
     const int b = rp[row], e = rp[row + 1];
     int k = b + lane;
@@ -25,12 +28,12 @@ __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int 
       const int j0 = ci[k], j1 = ci[k + T], j2 = ci[k + 2 * T], j3 = ci[k + 3 * T];
       const V a0 = val[k], a1 = val[k + T], a2 = val[k + 2 * T], a3 = val[k + 3 * T];
       const V x0 = __ldg(x + j0), x1 = __ldg(x + j1), x2 = __ldg(x + j2), x3 = __ldg(x + j3);
-      s = fma(a0, x0, s);
-      s = fma(a1, x1, s);
-      s = fma(a2, x2, s);
-      s = fma(a3, x3, s);
+      s = fma(sg * a0, x0, s);
+      s = fma(sg * a1, x1, s);
+      s = fma(sg * a2, x2, s);
+      s = fma(sg * a3, x3, s);
     }
-    for (; k < e; k += T) s = fma(val[k], __ldg(x + ci[k]), s);
+    for (; k < e; k += T) s = fma(sg * val[k], __ldg(x + ci[k]), s);
   }
 #pragma unroll
   for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
@@ -357,8 +360,8 @@ __global__ void __launch_bounds__(kBlock) k_jacobi(int n, const int *__restrict_
   CWM_TILE_LOOP(T, n) {
     const long long row = base + sub;
     const bool active = row < n;
-    const V dot = tile_row_dot<V, T>(rp, ci, val, x, row, active, lane);
-    if (active && lane == 0) y[row] = x[row] + dinv[row] * (b[row] - dot);
+    const V res = tile_row_dot<V, T, true>(rp, ci, val, x, row, active, lane, active && lane == 0 ? b[row] : V(0));
+    if (active && lane == 0) y[row] = fma(dinv[row], res, x[row]);
   }
 }
 
@@ -375,8 +378,8 @@ __global__ void __launch_bounds__(kBlock)
     const int nw = long_blocks * (kBlock / 32);
     for (int q = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); q < n_long; q += nw) {
       const int row = long_rows[q];
-      const V dot = tile_row_dot<V, 32>(rp, ci, val, x, row, true, lane);
-      if (lane == 0) y[row] = x[row] + dinv[row] * (b[row] - dot);
+      const V res = tile_row_dot<V, 32, true>(rp, ci, val, x, row, true, lane, lane == 0 ? b[row] : V(0));
+      if (lane == 0) y[row] = fma(dinv[row], res, x[row]);
     }
     return;
   }
@@ -388,8 +391,8 @@ __global__ void __launch_bounds__(kBlock)
   for (long long base = warp_id * kRowsPerWarp; base < n; base += nwarps * kRowsPerWarp) {
     const long long row = base + sub;
     const bool active = row < n && rp[row + 1] - rp[row] <= long_min;
-    const V dot = tile_row_dot<V, T>(rp, ci, val, x, row, active, lane);
-    if (active && lane == 0) y[row] = x[row] + dinv[row] * (b[row] - dot);
+    const V res = tile_row_dot<V, T, true>(rp, ci, val, x, row, active, lane, active && lane == 0 ? b[row] : V(0));
+    if (active && lane == 0) y[row] = fma(dinv[row], res, x[row]);
   }
 }
 
@@ -567,8 +570,8 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restric
   CWM_TILE_LOOP(T, n) {
     const long long row = base + sub;
     const bool active = row < n;
-    const V dot = tile_row_dot<V, T>(rp, ci, val, x, row, active, lane);
-    if (active && lane == 0) r[row] = b[row] - dot;
+    const V res = tile_row_dot<V, T, true>(rp, ci, val, x, row, active, lane, active && lane == 0 ? b[row] : V(0));
+    if (active && lane == 0) r[row] = x ? res : b[row];
   }
 }
 
