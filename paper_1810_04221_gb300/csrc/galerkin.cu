@@ -228,8 +228,57 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
 }
 
 // ------------------------------------------------------------ shared-memory rows ----
-// A coarse row with 32 < L <= kWarpCap entries: keys (J, slot) sorted in shared memory by
-// the warp (bitonic), runs of equal J summed in canonical order.
+// Bitonic sort of the warp's 32 * E keys held in registers, key q = lane * E + e: stages
+// with j < E compare within a lane, the others exchange with lane ^ (j / E) by shuffles.
+// All loops unroll, so the array stays in registers.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&a)[E], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < E) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int f = e ^ j;
+          if (f > e) {
+            const bool up = ((lane * E + e) & k) == 0;
+            const unsigned long long x = a[e], y = a[f];
+            if ((x > y) == up) { a[e] = y; a[f] = x; }
+          }
+        }
+      } else {
+        const int lm = j / E;
+        const bool lower = (lane & lm) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, a[e], lm);
+          const bool up = ((lane * E + e) & k) == 0;
+          a[e] = (lower == up) ? (a[e] < o ? a[e] : o) : (a[e] < o ? o : a[e]);
+        }
+      }
+    }
+  }
+}
+
+// Keys (J, slot) of a coarse row with L <= 32 * E entries, sorted into keys[0 .. 32E).
+template <int E>
+__device__ __forceinline__ void sort_row_keys(const RowSrc &r, int L, unsigned long long *keys,
+                                              const int *__restrict__ ci, const int *__restrict__ agg, int lane) {
+  unsigned long long a[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int q = lane * E + e;
+    a[e] = q < L ? make_key(r, q, ci, agg) : ~0ull;
+  }
+  warp_bitonic<E>(a, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) keys[lane * E + e] = a[e];
+  __syncwarp();
+}
+
+// A coarse row with 32 < L <= kWarpCap entries: keys (J, slot) sorted by the warp in
+// registers (bitonic), runs of equal J summed in canonical order.
 template <bool FILL, class Acc>
 __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsigned long long *keys,
                                                   const int *__restrict__ ci, const double *__restrict__ val,
@@ -239,21 +288,9 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
                                                   double *__restrict__ diag_c, int *err) {
   const int lane = threadIdx.x & 31;
   const int L = r.L1 + r.L2;
-  const int P = next_pow2(L < 32 ? 32 : L);
-  for (int q = lane; q < P; q += 32) keys[q] = q < L ? make_key(r, q, ci, agg) : ~0ull;
-  __syncwarp();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int q = lane; q < P; q += 32) {
-        const int l = q ^ j;
-        if (l > q) {
-          const unsigned long long a = keys[q], b = keys[l];
-          if ((a > b) == ((q & k) == 0)) { keys[q] = b; keys[l] = a; }
-        }
-      }
-      __syncwarp();
-    }
-  }
+  if (L <= 64) sort_row_keys<2>(r, L, keys, ci, agg, lane);
+  else if (L <= 128) sort_row_keys<4>(r, L, keys, ci, agg, lane);
+  else sort_row_keys<8>(r, L, keys, ci, agg, lane);
   int base = 0;
   for (int q0 = 0; q0 < L; q0 += 32) {
     const int q = q0 + lane;
