@@ -234,7 +234,10 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   F.sweep_mate.clear();
 
   for (int sweep = 0; sweep < S; ++sweep) {
-    CWM_TRY(edge_weights(cn, cnnz, crp, cci, cval, cdiag, cv, w.get(), dv.get(), s));
+    // every operator after the input is symmetric by construction (P^T A P of a symmetric
+    // A), so only the input's weights need the cleared array
+    CWM_TRY(edge_weights(cn, cnnz, crp, cci, cval, cdiag, cv, w.get(), dv.get(), s,
+                         h->lev.size() == 1 && sweep == 0));
     CWM_TRY(suitor_match(cn, cnnz, crp, cci, w.get(), skeys.get(), mate.get(),
                          default_cap(h->prm, cn, cnnz), h->err.get(), s));
     SweepOut o;

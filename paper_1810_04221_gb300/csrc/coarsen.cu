@@ -202,14 +202,16 @@ __global__ void k_vertex_dv(int n, const double *__restrict__ diag, const double
 }
 
 amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
-                        const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s) {
+                        const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s,
+                        bool clear) {
   if (n == 0) return AMG_OK;
   // rp, ci, val, w written; v and diag of each row (gathers of neighbours counted once)
   CWM_TRACE("weights", 4.0 * (n + 1) + 20.0 * nnz + 32.0 * n, s);
   k_vertex_dv<<<grid_for(n, 256, num_sms() * 8), 256, 0, s>>>(n, diag, v, dv_scratch);
   CWM_LAUNCH();
-  // lower slots without an upper partner (a pattern that is not symmetric) stay 0
-  CWM_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)nnz, s));
+  // lower slots without an upper partner (a pattern that is not symmetric) stay 0; a
+  // structurally symmetric pattern has every slot written, so the caller may skip this
+  if (clear) CWM_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)nnz, s));
   k_edge_weights_rb<<<(n + kWB - 1) / kWB, kWB, 0, s>>>(n, rp, ci, val, dv_scratch, v, w);
   CWM_LAUNCH();
   return AMG_OK;
@@ -385,26 +387,21 @@ amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, cons
 // iff it is unmatched or the smaller end of its pair, and the aggregate id is the number
 // of such leaders before i (an exclusive scan).  The leader writes both members' agg
 // and p, v_c, and the member list.
-__global__ void k_leader_flags(int n, const int *__restrict__ mate, int *__restrict__ flag) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int m = mate[i];
-  flag[i] = (m < 0 || i < m) ? 1 : 0;
-}
-
-// pairs counted with one atomic per block
-__global__ void k_count_pairs(int n, const int *__restrict__ mate, int *npairs) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int is_pair = (i < n && mate[i] > i) ? 1 : 0;
-  int c = __syncthreads_count(is_pair);
+// Leader flags, and the pairs counted with one atomic per block.
+__global__ void k_leader_flags(int n, const int *__restrict__ mate, int *__restrict__ flag, int *npairs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = i < n ? mate[i] : -1;
+  if (i < n) flag[i] = (m < 0 || i < m) ? 1 : 0;
+  const int c = __syncthreads_count(i < n && m > i);
   if (threadIdx.x == 0 && c) atomicAdd(npairs, c);
 }
 
 __global__ void k_aggregate_fill(int n, const int *__restrict__ mate, const int *__restrict__ id,
                                  const double *__restrict__ v, int *__restrict__ agg,
                                  double *__restrict__ p, double *__restrict__ vc,
-                                 int *__restrict__ m1, int *__restrict__ m2) {
+                                 int *__restrict__ m1, int *__restrict__ m2, int *__restrict__ nc_out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *nc_out = id[n];  // the number of aggregates (the scan's total)
   if (i >= n) return;
   const int j = mate[i];
   if (j >= 0 && j < i) return;  // the follower is written by its leader
@@ -436,13 +433,10 @@ amg_status aggregate(int n, const int *mate, const double *v, int *agg, double *
   if (n == 0) return AMG_OK;
   CWM_TRACE("aggregate", 52.0 * n, s);
   const int g = grid_for(n, 256, 1 << 30);
-  k_leader_flags<<<g, 256, 0, s>>>(n, mate, id_scratch);
-  CWM_LAUNCH();
-  k_count_pairs<<<g, 256, 0, s>>>(n, mate, d_counts + 1);
+  k_leader_flags<<<g, 256, 0, s>>>(n, mate, id_scratch, d_counts + 1);
   CWM_LAUNCH();
   CWM_TRY(exclusive_scan(id_scratch, id_scratch, n, scan_scratch, s));
-  CWM_CUDA(cudaMemcpyAsync(d_counts, id_scratch + n, sizeof(int), cudaMemcpyDeviceToDevice, s));
-  k_aggregate_fill<<<g, 256, 0, s>>>(n, mate, id_scratch, v, agg, p, vc, m1, m2);
+  k_aggregate_fill<<<g, 256, 0, s>>>(n, mate, id_scratch, v, agg, p, vc, m1, m2, d_counts);
   CWM_LAUNCH();
   return AMG_OK;
 }

@@ -20,7 +20,8 @@ amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, 
                         int *d_err, cudaStream_t s);
 // dv_scratch: n doubles (per-vertex (a_ii v_i) v_i)
 amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
-                        const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s);
+                        const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s,
+                        bool clear = true);
 size_t suitor_scratch_bytes(int n);
 amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, const double *w,
                         void *scratch, int *mate, long long cap, int *d_err, cudaStream_t s);

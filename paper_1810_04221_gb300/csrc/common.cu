@@ -260,9 +260,47 @@ __global__ void k_scan_down(const int *__restrict__ in, int *__restrict__ out, l
   if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = bsum[nb];
 }
 
+// Small inputs in one launch: one block of kScanOneThreads threads walks the input in
+// chunks of kScanOneThreads * kScanOneItems (each thread a run of consecutive items),
+// carrying the running total; out[n] = the total.  (The setup's small levels are bound
+// by launch latency, where three launches per scan cost more than the scan.)
+static constexpr int kScanOneThreads = 1024;
+static constexpr int kScanOneItems = 16;
+static constexpr long long kScanOneMax = 16384;  // one chunk: at 32K-64K the sequential chunks lost to three launches (measured)
+
+// in and out may be the same array (each chunk is read before the block scan's barriers
+// and written after them).
+__global__ void __launch_bounds__(kScanOneThreads) k_scan_one(const int *in, int *out, int n) {
+  int carry = 0;
+  for (int base = 0; base < n; base += kScanOneThreads * kScanOneItems) {
+    const int first = base + threadIdx.x * kScanOneItems;
+    int vals[kScanOneItems];
+    int sum = 0;
+#pragma unroll
+    for (int t = 0; t < kScanOneItems; ++t) {
+      vals[t] = first + t < n ? in[first + t] : 0;
+      sum += vals[t];
+    }
+    int total;
+    int ex = carry + block_excl_scan(sum, &total);
+#pragma unroll
+    for (int t = 0; t < kScanOneItems; ++t) {
+      if (first + t < n) out[first + t] = ex;
+      ex += vals[t];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
 amg_status exclusive_scan(const int *in, int *out, long long n, int *scratch, cudaStream_t s) {
   if (n <= 0) {
     CWM_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+    return AMG_OK;
+  }
+  if (n <= kScanOneMax) {
+    k_scan_one<<<1, kScanOneThreads, 0, s>>>(in, out, (int)n);
+    CWM_LAUNCH();
     return AMG_OK;
   }
   int nb = (int)((n + kScanChunk - 1) / kScanChunk);

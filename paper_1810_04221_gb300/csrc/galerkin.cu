@@ -478,8 +478,9 @@ static amg_status galerkin_attrs() {
 // cnt[I] = L1 + L2: the number of fine entries that coarse row I gathers, an upper bound
 // on its length (its padded row length).
 __global__ void k_gather_lengths(int nc, const int *__restrict__ rp, const int *__restrict__ m1,
-                                 const int *__restrict__ m2, int *__restrict__ cnt) {
+                                 const int *__restrict__ m2, int *__restrict__ cnt, int *__restrict__ n_long) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I == 0) *n_long = 0;  // the long-row queue starts empty
   if (I >= nc) return;
   const int i1 = m1[I], i2 = m2[I];
   cnt[I] = rp[i1 + 1] - rp[i1] + (i2 >= 0 ? rp[i2 + 1] - rp[i2] : 0);
@@ -513,12 +514,11 @@ amg_status galerkin_group(const int *rp, const int *ci, const double *val, int n
   // members and row bounds, ci, agg(ci), val and p of both member rows; the padded rows
   // written (columns and values), the counts and both scans
   CWM_TRACE("galerkin", 16.0 * work.nnz_fine + 16.0 * work.n_fine + 72.0 * nc + 12.0 * work.nnz_fine, s);
-  k_gather_lengths<<<grid_for(nc, 256, 1 << 30), 256, 0, s>>>(nc, rp, m1, m2, work.cnt);
+  k_gather_lengths<<<grid_for(nc, 256, 1 << 30), 256, 0, s>>>(nc, rp, m1, m2, work.cnt, work.n_long);
   CWM_LAUNCH();
   CWM_TRY(exclusive_scan(work.cnt, work.rpu, nc, work.scan, s));
   const int block = kWarpsPerBlock * 32;
   const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
-  CWM_CUDA(cudaMemsetAsync(work.n_long, 0, sizeof(int), s));
   if (fp32) {
     k_galerkin_warp<true, float><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
                                                         work.ci_pad, work.val_pad, diag_c, work.long_rows,
