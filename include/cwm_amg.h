@@ -52,7 +52,10 @@ typedef struct {
   int vcycle_fp32;      /* 1: the V-cycle runs on float32 copies of the hierarchy values
                            (FCG recurrences stay float64); 0: all float64 (default 0) */
   int check_input;      /* 1: amg_setup verifies CSR structure and bit symmetry of A on
-                           the device before coarsening (default 1) */
+                           the device before coarsening (default 1).  0: the caller
+                           vouches for both; the coarse operators' edge weights then
+                           rely on the symmetric pattern (an unchecked non-symmetric
+                           input gives an undefined, though terminating, hierarchy) */
   int keep_sweeps;      /* 1: keep every sweep's matching for amg_sweep_mate (default 0) */
   int64_t loop_cap;     /* cap on iterations of any one device retry loop or wait (Suitor
                            proposal chains, grid-barrier polls in the V-cycle); 0 = derived
