@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <mutex>
+#include <vector>
 
 #include "trace.cuh"
 
@@ -154,6 +155,29 @@ void retain_pool_memory() {
   uint64_t thr = UINT64_MAX;
   cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   (void)cudaGetLastError();
+}
+
+int resident_blocks(const void *kernel, int block, size_t smem) {
+  struct Key {
+    int dev;
+    const void *k;
+    int block;
+    size_t smem;
+  };
+  static std::mutex mu;
+  static std::vector<std::pair<Key, int>> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto &e : cache)
+    if (e.first.dev == dev && e.first.k == kernel && e.first.block == block && e.first.smem == smem) return e.second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cache.push_back({Key{dev, kernel, block, smem}, n});
+  return n;
 }
 
 int num_sms() {

@@ -79,6 +79,17 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Blocks of `block` threads of a kernel that fit on one SM at once (occupancy API, cached
+// per device and kernel).  A grid-stride kernel whose grid assumes more resident blocks
+// than its registers allow runs a second, partly empty wave; wave_cap bounds its grid.
+int resident_blocks(const void *kernel, int block, size_t smem);
+template <class K>
+inline int wave_cap(K kernel, int grid, int block, size_t smem = 0) {
+  const int r = resident_blocks(reinterpret_cast<const void *>(kernel), block, smem);
+  const int cap = r > 0 ? r * num_sms() : grid;
+  return grid < cap ? grid : cap;
+}
+
 // Launch-error check after a kernel launch; also counts the library's kernel launches.
 void count_launch();
 #define CWM_LAUNCH()         \

@@ -540,7 +540,8 @@ amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const 
                           cudaStream_t s) {
   if (n == 0) return AMG_OK;
   CWM_TRACE("prolong", (4.0 + 4.0 * sizeof(V)) * n, s);
-  CWM_CUDA(launch_pdl(k_prolong_scaled<V>, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, agg, p, xc, dinv, b, y));
+  CWM_CUDA(launch_pdl(k_prolong_scaled<V>, wave_cap(k_prolong_scaled<V>, grid_for(n, kBlock, num_sms() * 8), kBlock), kBlock,
+                      0, s, n, agg, p, xc, dinv, b, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -648,7 +649,8 @@ amg_status resid_restrict(const CsrView<V> &A, int nc, const int *mptr, const in
   if (nc == 0) return AMG_OK;
   CWM_TRACE("resid_restrict", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + (3.0 * sizeof(V) + 4.0) * A.n +
                                   (4.0 + sizeof(V)) * nc, s);
-  CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_resid_restrict<V, kT>, rows_grid(nc, kT), kBlock, 0, s, nc, A.rp, A.ci, A.val, mptr,
+  CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_resid_restrict<V, kT>, wave_cap(k_resid_restrict<V, kT>, rows_grid(nc, kT), kBlock),
+                                             kBlock, 0, s, nc, A.rp, A.ci, A.val, mptr,
                                                                                       mlist, p, b, x, bc)));
   CWM_LAUNCH();
   return AMG_OK;
@@ -1061,7 +1063,8 @@ amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const do
                                                           first));
   } else {
     // at most num_sms() * 8 blocks (rows_grid), within fcg_dots_blocks_max
-    CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_spmv_dots_tile<kT>, rows_grid(A.n, kT), kBlock, 0, s, A.n, A.rp, A.ci, A.val, w, r,
+    CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_spmv_dots_tile<kT>, wave_cap(k_spmv_dots_tile<kT>, rows_grid(A.n, kT), kBlock),
+                                               kBlock, 0, s, A.n, A.rp, A.ci, A.val, w, r,
                                                                                     q, v, part, scal, tick, first)));
   }
   CWM_LAUNCH();
