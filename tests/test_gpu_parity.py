@@ -146,6 +146,56 @@ def test_galerkin_long_rows_block_path():
     assert bits_equal(host(valc), valc_r)
 
 
+def _graded_graph(seed=11):
+    """Random s.p.d. graph made of diagonal blocks of growing density (mean degrees 4 to
+    ~200) joined by a few edges, so that the coarse rows of a pairwise aggregation gather
+    from under 16 to over 256 fine entries."""
+    rng = np.random.default_rng(seed)
+    import scipy.sparse as sp
+    blocks = [(3000, 4), (1000, 12), (600, 25), (400, 50), (400, 100), (500, 220)]
+    rows, cols, base = [], [], 0
+    for nb, deg in blocks:
+        m = nb * deg // 2
+        rows.append(base + rng.integers(0, nb, m))
+        cols.append(base + rng.integers(0, nb, m))
+        base += nb
+    n = base
+    rows.append(rng.integers(0, n, 200))
+    cols.append(rng.integers(0, n, 200))
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    keep = r != c
+    A = sp.coo_matrix((-rng.uniform(0.1, 1.0, keep.sum()), (r[keep], c[keep])), shape=(n, n)).tocsr()
+    A = 0.5 * (A + A.T)
+    A.sum_duplicates()
+    d = np.asarray(abs(A).sum(axis=1)).ravel() + rng.uniform(0.1, 1.0, n)
+    A = sp.csr_matrix(A + sp.diags(d))
+    A.sort_indices()
+    return A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64)
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_galerkin_all_row_paths(fp32):
+    """Coarse rows of every length class -- registers (<= 16, <= 32 entries), the warp's
+    register sort with 2, 4 and 8 keys per lane (<= 64, <= 128, <= 256) and the block kernel
+    (> 256) -- against the oracle, bit for bit (float64 and binary32 products)."""
+    mat = _graded_graph()
+    n = len(mat[0]) - 1
+    v = np.ones(n)
+    w = oracle.edge_weights(*mat, v)
+    mate = oracle.greedy_match(mat[0], mat[1], w)
+    agg, nc, _, _ = oracle.aggregate(mate)
+    lens = np.diff(mat[0])
+    L = np.bincount(agg, weights=lens, minlength=nc).astype(int)
+    for lo, hi in [(1, 16), (17, 32), (33, 64), (65, 128), (129, 256), (257, 10**6)]:
+        assert ((L >= lo) & (L <= hi)).any(), (lo, hi)
+    p, _ = oracle.prolongator(agg, nc, v)
+    rpc_r, cic_r, valc_r = oracle.galerkin(*mat, agg, nc, p, fp32=bool(fp32))
+    rp, ci, val = csr_dev(*mat)
+    rpc, cic, valc = B.cwm_galerkin(rp, ci, val, nc, dev(agg), dev(p), fp32=fp32)
+    assert np.array_equal(host(rpc), rpc_r) and np.array_equal(host(cic), cic_r)
+    assert bits_equal(host(valc), valc_r)
+
+
 # ------------------------------------------------------------------ hierarchy ----
 
 HIER_CASES = [
