@@ -44,7 +44,8 @@ typedef enum {
 typedef struct {
   int sweeps_per_level; /* pairwise matching sweeps composed per level: 1, 2, 3 give
                            aggregates of at most 2, 4, 8 (default 2, Sec. 5) */
-  int coarse_max;       /* stop coarsening once n <= coarse_max (default 40) */
+  int coarse_max;       /* stop coarsening once n <= coarse_max (default 40); -1: the
+                           paper's setting floor(40 n^(1/3)) of the input size n (Sec. 5) */
   int max_levels;       /* at most this many levels, finest included (default 40) */
   int pre_sweeps;       /* l1-Jacobi sweeps before the coarse correction (default 1) */
   int post_sweeps;      /* l1-Jacobi sweeps after it (default 1) */

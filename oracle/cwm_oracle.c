@@ -418,6 +418,20 @@ void or_free(or_hier *h) {
   free(h);
 }
 
+/* The paper's default coarse size (Sec. 5, solver settings): floor(40 n^(1/3)), taken as
+ * the largest m with m^3 <= 64000 n (40^3 = 64000), by bisection on integers so that no
+ * rounding of a floating cube root enters. */
+int or_paper_coarse_max(int n) {
+  const long long X = 64000LL * (long long)n;
+  long long lo = 0, hi = 1LL << 21;  /* hi^3 > 64000 * 2^31 */
+  while (lo < hi) {
+    const long long mid = (lo + hi + 1) / 2;
+    if (mid * mid * mid <= X) lo = mid;
+    else hi = mid - 1;
+  }
+  return (int)lo;
+}
+
 /* Build the hierarchy: levels while n_k > coarse_max and nl < max_levels; each level
  * does `sweeps` pairwise matching sweeps; stops early when a sweep forms no pair, and,
  * when stall_ratio > 0, after a level whose coarsening ratio n_k / n_{k+1} is below it.
@@ -427,7 +441,8 @@ or_hier *or_setup(int n, const int *rp, const int *ci, const double *val, const 
                   int sweeps, int coarse_max, int max_levels, double stall_ratio,
                   int galerkin_fp32_from, int *status) {
   *status = OR_OK;
-  if (n <= 0 || sweeps < 1 || sweeps > OR_MAX_SWEEPS || max_levels < 1 ||
+  if (coarse_max == -1 && n > 0) coarse_max = or_paper_coarse_max(n);  /* -1: the paper's default */
+  if (n <= 0 || sweeps < 1 || sweeps > OR_MAX_SWEEPS || max_levels < 1 || coarse_max < 0 ||
       max_levels > OR_MAX_LEVELS || or_check_csr(n, rp, ci) != OR_OK) {
     *status = OR_ERR_ARG;
     return NULL;

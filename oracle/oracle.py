@@ -51,6 +51,7 @@ def _load():
         vp, i, l, d = C.c_void_p, C.c_int, C.c_long, C.c_double
         sig = {
             "or_check_csr": (i, [i, _i32p, _i32p]),
+            "or_paper_coarse_max": (i, [i]),
             "or_check_symmetric": (i, [i, _i32p, _i32p, _f64p]),
             "or_edge_weights": (i, [i, _i32p, _i32p, _f64p, _f64p, _f64p]),
             "or_greedy_match": (i, [i, _i32p, _i32p, _f64p, _i32p]),
@@ -167,6 +168,12 @@ def galerkin(rp, ci, val, agg, nc, p, fp32=False):
     if lib.or_galerkin(n, rp, ci, val, nc, agg, p, 1 if fp32 else 0, rpc, cic, valc) != OK:
         raise MemoryError
     return rpc, cic, valc
+
+
+def paper_coarse_max(n: int) -> int:
+    """The paper's coarse size for an input of n rows (Sec. 5): floor(40 n^(1/3));
+    Hierarchy(coarse_max=-1) uses it."""
+    return int(_load().or_paper_coarse_max(int(n)))
 
 
 class Hierarchy:

@@ -626,6 +626,16 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   P.trace_filter[sizeof(P.trace_filter) - 1] = '\0';
   h->trace.filter = P.trace_filter;
   TraceGuard tg(h);
+  if (P.coarse_max == -1) {  // the paper's default (Sec. 5): floor(40 n^(1/3)) = icbrt(64000 n)
+    const long long X = 64000LL * (long long)n;
+    long long lo = 0, hi = 1LL << 21;
+    while (lo < hi) {
+      const long long mid = (lo + hi + 1) / 2;
+      if (mid * mid * mid <= X) lo = mid;
+      else hi = mid - 1;
+    }
+    P.coarse_max = (int)lo;
+  }
   if (P.sweeps_per_level < 1 || P.sweeps_per_level > kMaxSweeps || P.max_levels < 1 || P.pre_sweeps < 0 ||
       P.post_sweeps < 0 || P.coarse_sweeps < 0 || P.coarse_max < 0 || P.galerkin_fp32_from < 0) {
     set_error("amg_setup: parameter out of range");

@@ -389,3 +389,18 @@ def test_vcycle_barrier_wait_reports_timeout():
     st, info = B.amg_pcg_solve(h, dev(np.ones(256)), x)
     assert st == B.AMG_OK
     h.free()
+
+
+def test_paper_coarse_size_matches_oracle():
+    """coarse_max = -1 (the paper's floor(40 n^(1/3))): the same levels as the oracle."""
+    mat = P.poisson3d(32)
+    n = len(mat[0]) - 1
+    H = oracle.Hierarchy(*mat, np.ones(n), sweeps=3, coarse_max=-1)
+    h = B.amg_setup(*csr_dev(*mat), dev(np.ones(n)), B.amg_default_params(sweeps_per_level=3, coarse_max=-1))
+    try:
+        assert B.amg_num_levels(h) == H.nl == 3
+        for k in range(H.nl):
+            got, ref = B.amg_level_export(h, k), H.level(k)
+            assert np.array_equal(host(got["ci"]), ref["ci"]) and bits_equal(host(got["val"]), ref["val"])
+    finally:
+        h.free()

@@ -200,6 +200,26 @@ def test_hierarchy_composed_prolongator(sweeps):
             np.abs(F["dl1"] - np.asarray(abs(A).sum(axis=1)).ravel()).max() < 1e-13 * F["dl1"].max()
 
 
+def test_paper_coarse_size():
+    """The paper's coarse size floor(40 n^(1/3)) (Sec. 5): exactly 40 k for n = k^3, and the
+    defining bounds m^3 <= 64000 n < (m + 1)^3 elsewhere."""
+    for k in (1, 2, 16, 100, 128, 160):
+        assert oracle.paper_coarse_max(k ** 3) == 40 * k
+    for n in (2, 3, 999, 1001, 4095, 4097, 786432, 884736, 4096000 - 1, 2 ** 31 - 1):
+        m = oracle.paper_coarse_max(n)
+        assert m ** 3 <= 64000 * n < (m + 1) ** 3, n
+
+
+def test_hierarchy_paper_coarse_size():
+    """coarse_max = -1 stops where the paper's rule does: 3D Poisson 32^3 (n = 32768, coarse
+    size 1280) keeps the 4096-row level (> 1280) and stops at 512 rows."""
+    rp, ci, val = P.poisson3d(32)
+    H = oracle.Hierarchy(rp, ci, val, np.ones(32 ** 3), sweeps=3, coarse_max=-1)
+    assert [H.level_n(k) for k in range(H.nl)] == [32768, 4096, 512]
+    H2 = oracle.Hierarchy(rp, ci, val, np.ones(32 ** 3), sweeps=3, coarse_max=4096)
+    assert H2.nl == 2
+
+
 def test_hierarchy_stops_without_pairs():
     # diagonal matrix: no edge, so no coarse level is made
     n = 50
