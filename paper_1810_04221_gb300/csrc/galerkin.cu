@@ -6,13 +6,14 @@
 // repeated the whole grouping -- the sorts of long rows included -- only to size the
 // output.)
 //
-// Coarse row I has members i1 < i2 (or i1 alone).  The fine entries of rows i1 and i2 are
-// keyed by (J = agg(j), local slot) and sorted in shared memory (bitonic), so equal J are
-// adjacent.  Each run of equal J holds at most four terms (two members each side); the
-// run's value sums t_ij = (p_i p_j) a_ij from +0.0 in ascending (min(i,j), max(i,j), i)
-// order with round-to-nearest intrinsics, which makes the result independent of the
-// thread schedule and bit-symmetric.  Rows gathering more than kWarpCap entries go to a
-// block-per-row kernel (up to kBlockCap entries).  The fill pass has a binary32 variant
+// Coarse row I has members i1 < i2 (or i1 alone).  Rows of at most 32 entries group equal
+// J = agg(j) in registers (__match_any_sync); longer ones key their fine entries by
+// (J, local slot) and sort them (bitonic: in registers by a warp up to kWarpCap entries,
+// in shared memory by a block beyond, up to kBlockCap entries), so equal J are adjacent.
+// Each run of equal J holds at most four terms (two members each side); the run's value
+// sums t_ij = (p_i p_j) a_ij from +0.0 in ascending (min(i,j), max(i,j), i) order with
+// round-to-nearest intrinsics, which makes the result independent of the thread schedule
+// and bit-symmetric.  The grouping has a binary32 variant
 // (Acc = float): p_i, p_j and a_ij rounded to float, terms and sums in float in the same
 // order, each entry stored as the double of its float.
 #include <climits>
@@ -21,7 +22,7 @@
 
 namespace cwm {
 
-constexpr int kWarpCap = 256;     // keys per warp in shared memory
+constexpr int kWarpCap = 256;     // keys per warp (sorted in registers, kept in shared memory)
 constexpr int kWarpsPerBlock = 8;
 constexpr int kBlockCap = 8192;   // keys per long row (64 KB of dynamic shared memory)
 constexpr int kLongThreads = 256;
@@ -140,7 +141,7 @@ __device__ __forceinline__ int next_pow2(int x) {
 // sort is needed: the lowest lane of each equal-J group leads it, counts it, and in the
 // fill pass gathers the group's (at most four) terms with shuffles, orders them by
 // (min(i,j), max(i,j), i), sums them from +0.0, and writes at its rank among the leaders.
-template <bool FILL, class Acc>
+template <class Acc>
 __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigned gmask, int gbase, int glen,
                                                  const int *__restrict__ ci, const double *__restrict__ val,
                                                  const int *__restrict__ agg, const double *__restrict__ p,
@@ -164,7 +165,6 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
   const bool leader = act && lane == __ffs(mm) - 1;
   const unsigned lead = __ballot_sync(gmask, leader) & gmask;
   if (gl == 0 && cnt) cnt[I] = __popc(lead);
-  if (!FILL) return;
   Acc t = Acc(0);
   int kmin = 0, kmax = 0;
   if (act) {
@@ -279,7 +279,7 @@ __device__ __forceinline__ void sort_row_keys(const RowSrc &r, int L, unsigned l
 
 // A coarse row with 32 < L <= kWarpCap entries: keys (J, slot) sorted by the warp in
 // registers (bitonic), runs of equal J summed in canonical order.
-template <bool FILL, class Acc>
+template <class Acc>
 __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsigned long long *keys,
                                                   const int *__restrict__ ci, const double *__restrict__ val,
                                                   const int *__restrict__ agg, const double *__restrict__ p,
@@ -301,7 +301,7 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
       head = q == 0 || (unsigned)(keys[q - 1] >> 32) != J;
     }
     const unsigned ball = __ballot_sync(0xffffffffu, head);
-    if (FILL && head) {
+    if (head) {
       int len = 1;
       while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
       if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
@@ -320,9 +320,11 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
 // ------------------------------------------------------------ warp kernel ----
 // Each warp takes two consecutive coarse rows.  When both gather <= 16 entries each half
 // warp handles one in registers; otherwise the warp handles them in turn (registers up to
-// 32 entries, shared memory up to kWarpCap, longer rows queued for the block kernel).
-// FILL = false: cnt[I] = number of distinct J.  FILL = true: columns and values at rpc[I].
-template <bool FILL, class Acc>
+// 32 entries, the warp's register sort up to kWarpCap, longer rows queued for the block
+// kernel).
+// Columns and values of row I at rpc[I] (the padded offsets), and cnt[I] = its number of
+// distinct J.
+template <class Acc>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_galerkin_warp(int nc, const int *__restrict__ rp, const int *__restrict__ ci,
                     const double *__restrict__ val, const int *__restrict__ m1,
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int L0 = __shfl_sync(0xffffffffu, Lh, 0), L1 = __shfl_sync(0xffffffffu, Lh, 16);
     if (L0 <= 16 && L1 <= 16) {
       if (Ih < nc)
-        galerkin_row_reg<FILL, Acc>(rh, Ih, half ? 0xffff0000u : 0x0000ffffu, half * 16, 16, ci, val, agg, p, cnt, rpc,
+        galerkin_row_reg<Acc>(rh, Ih, half ? 0xffff0000u : 0x0000ffffu, half * 16, 16, ci, val, agg, p, cnt, rpc,
                                cic, valc, diag_c, err);
       __syncwarp();
       continue;
@@ -358,9 +360,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const RowSrc r = row_src(I, m1, m2, rp);
       const int L = r.L1 + r.L2;
       if (L <= 32) {
-        galerkin_row_reg<FILL, Acc>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+        galerkin_row_reg<Acc>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (L <= kWarpCap) {
-        galerkin_row_smem<FILL, Acc>(r, I, keys, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+        galerkin_row_smem<Acc>(r, I, keys, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (long_rows && lane == 0) {
         long_rows[atomicAdd(n_long, 1)] = I;
       }
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 // ------------------------------------------------------------ long rows ----
-template <bool FILL, class Acc>
+template <class Acc>
 __global__ void __launch_bounds__(kLongThreads)
     k_galerkin_block(const int *__restrict__ rp, const int *__restrict__ ci,
                      const double *__restrict__ val, const int *__restrict__ m1,
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(kLongThreads)
         if (w < warp) before += wsum[w];
         chunk += wsum[w];
       }
-      if (FILL && head) {
+      if (head) {
         int len = 1;
         while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
         if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(kLongThreads)
       __syncthreads();
     }
     if (cnt && tid == 0) cnt[I] = base;
-    if (FILL && dl1_c) {
+    if (dl1_c) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
       if (lane == 0) wl1[warp] = l1;
@@ -464,11 +466,9 @@ static amg_status galerkin_attrs() {
   CWM_CUDA(cudaGetDevice(&dev));
   bool &attr = attr_set[dev & 63];
   if (!attr) {
-    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kBlockCap * 8));
-    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kBlockCap * 8));
-    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CWM_CUDA(cudaFuncSetAttribute(k_galerkin_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kBlockCap * 8));
     attr = true;
   }
@@ -520,19 +520,19 @@ amg_status galerkin_group(const int *rp, const int *ci, const double *val, int n
   const int block = kWarpsPerBlock * 32;
   const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
   if (fp32) {
-    k_galerkin_warp<true, float><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
+    k_galerkin_warp<float><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
                                                         work.ci_pad, work.val_pad, diag_c, work.long_rows,
                                                         work.n_long, d_err);
     CWM_LAUNCH();
-    k_galerkin_block<true, float><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+    k_galerkin_block<float><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
         rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu, work.ci_pad, work.val_pad, diag_c, dl1_c,
         work.long_rows, work.n_long, d_err);
   } else {
-    k_galerkin_warp<true, double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
+    k_galerkin_warp<double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
                                                          work.ci_pad, work.val_pad, diag_c, work.long_rows,
                                                          work.n_long, d_err);
     CWM_LAUNCH();
-    k_galerkin_block<true, double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
+    k_galerkin_block<double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
         rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu, work.ci_pad, work.val_pad, diag_c, dl1_c,
         work.long_rows, work.n_long, d_err);
   }
