@@ -82,6 +82,17 @@ typedef struct {
                            sums in float in the canonical order, stored as doubles (the
                            precision trade-off of Sec. 3.2 carried over to the setup; the
                            finest operator stays the caller's); 0 = off (default) */
+  int coupled_post;     /* coarse correction + the post-sweep (post_sweeps = 1) as one pass
+                           over the stored product A^k P^k: since b - A(xs + P xc) =
+                           (b - A xs) - (A P) xc and the restriction already formed
+                           b - A xs, the sweep streams A P (one column per aggregate)
+                           instead of A and the separate prolongation pass goes.
+                           0 = auto (default: levels with more than 16 entries per row
+                           on average that do not take the fused small-level kernels;
+                           on short rows building A P costs about what one solve
+                           gains); 1 = every level below the coarsest;
+                           -1 = off.  Levels with rows longer than 1024 entries never
+                           take it. */
 } amg_params;
 
 /* Statistics filled by amg_pcg_solve and amg_stats. */

@@ -47,6 +47,7 @@ class AmgParams(C.Structure):
         ("stall_ratio", C.c_double),
         ("gamma", C.c_int),
         ("galerkin_fp32_from", C.c_int),
+        ("coupled_post", C.c_int),
     ]
 
 

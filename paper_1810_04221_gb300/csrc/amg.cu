@@ -43,6 +43,13 @@ struct Level {
   // rows longer than long_min, taken by a whole warp in the l1-Jacobi sweep (n_long = 0: none)
   DBuf<int> long_rows;
   int n_long = 0, long_min = 0;
+  // A P (n rows, one column per aggregate of the next level; empty: not built), for the
+  // coarse correction + post-sweep of cycle_level
+  DBuf<int> ap_rp, ap_ci;
+  DBuf<double> ap_val;
+  DBuf<float> ap_val32;
+  long long ap_nnz = 0;
+  int ap_max_row = 0;
 
   template <class V>
   void split(CsrView<V> &a, bool fp64) const {
@@ -66,6 +73,14 @@ struct Level {
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get();
     row_kernel_shape(n, nnz, max_row, false, &a.rb, &a.tile);
     split(a, false);
+    return a;
+  }
+  template <class V>
+  CsrView<V> ap_view(const V *values) const {
+    CsrView<V> a;
+    a.n = n; a.nnz = ap_nnz; a.rp = ap_rp.get(); a.ci = ap_ci.get(); a.val = values;
+    a.max_row = ap_max_row;
+    row_kernel_shape(n, ap_nnz, ap_max_row, sizeof(V) == 8, &a.rb, &a.tile);
     return a;
   }
 };
@@ -328,6 +343,99 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   return AMG_OK;
 }
 
+// Largest level whose cycle uses the fused kernels (see cycle_level), per precision.  The
+// fused forms rebuild x_j per nonzero (D^{-1} b, and D^{-1} b + P x_c), two or three FP64
+// operations per nonzero instead of one; where GB300's FP64 pipe binds, that costs more
+// than the passes saved.  3D Poisson 128^3, FP64 V-cycle: limits of 300000 / 65536 / 0 rows
+// gave 11.61 / 11.41 / 11.62 ms per solve (level 1 has 262,144 rows).
+#ifndef CWM_FUSE_MAX_ROWS64
+#define CWM_FUSE_MAX_ROWS64 65536
+#endif
+template <class V>
+constexpr int fuse_max_rows() { return sizeof(V) == 8 ? CWM_FUSE_MAX_ROWS64 : 300000; }
+
+// Longest row of A for which A P is built (its grouping searches the row's list of
+// aggregates once per chunk of 32 entries).
+constexpr int kApMaxRow = 1024;
+
+// In auto mode A P is built for levels whose mean row is longer than this.  Measured on
+// GB300 (setup + one solve): Q1 elasticity 64^3 (78 entries per row, A P about a third of
+// that) 71.4 -> 68.8 ms; on the 7-entry rows of 3D Poisson 128^3 and the lognormal 160^3
+// levels the solve gained what building A P cost (FP64 17.98 -> 18.01 ms, FP32 16.18 ->
+// 16.24 ms, lognormal 44.9 -> 45.5 ms), so short-row levels keep the separate passes.
+constexpr double kApAutoMinMean = 16.0;
+
+// Whether level L gets A P (see build_ap).
+bool wants_ap(const amg_hierarchy *h, const Level &L) {
+  const amg_params &P = h->prm;
+  if (!L.agg.get() || P.coupled_post < 0 || P.post_sweeps != 1 || L.max_row > kApMaxRow || L.nnz == 0) return false;
+  if (P.coupled_post == 1) return true;
+  // auto: long-row levels that do not take the fused small-level kernels
+  if ((double)L.nnz <= kApAutoMinMean * L.n) return false;
+  const bool f32 = P.vcycle_fp32 != 0;
+  bool rb = true;
+  int t = 0;
+  row_kernel_shape(L.n, L.nnz, L.max_row, !f32, &rb, &t);
+  const int lim = f32 ? fuse_max_rows<float>() : fuse_max_rows<double>();
+  return !(P.pre_sweeps == 1 && rb && L.n <= lim);
+}
+
+// Builds A P for the levels that take the coarse correction and their post-sweep through it
+// (cycle_level): with y = xs + P xc, b - A y = (b - A xs) - (A P) xc, and the residual
+// b - A xs is the one the restriction already formed, so the sweep streams A P (one entry per
+// aggregate met in a row) instead of A, and the separate prolongation pass goes.  Every
+// level's rows are grouped first, then one synchronisation reads the sizes, then the rows are
+// compacted.
+amg_status build_ap(amg_hierarchy *h) {
+  cudaStream_t s = h->stream;
+  std::vector<int> todo;
+  for (int k = 0; k + 1 < (int)h->lev.size(); ++k)
+    if (wants_ap(h, h->lev[k])) todo.push_back(k);
+  if (todo.empty()) return AMG_OK;
+  const size_t m = todo.size();
+  std::vector<DBuf<int>> ci_pad(m);
+  std::vector<DBuf<double>> val_pad(m);
+  DBuf<int> cnt, scan, stat;  // stat: per level, nnz(A P) and its longest row
+  int nmax = 0;
+  for (int k : todo) nmax = std::max(nmax, h->lev[k].n);
+  CWM_TRY(cnt.alloc((size_t)nmax + 1, s));
+  CWM_TRY(scan.alloc(scan_scratch_ints(nmax), s));
+  CWM_TRY(stat.alloc(2 * m, s));
+  CWM_CUDA(cudaMemsetAsync(stat.get(), 0, 2 * m * sizeof(int), s));
+  for (size_t q = 0; q < m; ++q) {
+    Level &L = h->lev[todo[q]];
+    LevelTag tag(todo[q]);
+    CWM_TRY(ci_pad[q].alloc(L.nnz, s));
+    CWM_TRY(val_pad[q].alloc(L.nnz, s));
+    CWM_TRY(L.ap_rp.alloc((size_t)L.n + 1, s));
+    CWM_TRY(ap_group(L.n, L.nnz, L.rp.get(), L.ci.get(), L.val.get(), L.agg.get(), L.p.get(), L.max_row,
+                     ci_pad[q].get(), val_pad[q].get(), cnt.get(), stat.get() + 2 * q + 1, s));
+    CWM_TRY(exclusive_scan(cnt.get(), L.ap_rp.get(), L.n, scan.get(), s));
+    CWM_CUDA(cudaMemcpyAsync(stat.get() + 2 * q, L.ap_rp.get() + L.n, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  }
+  std::vector<int> hs(2 * m);
+  CWM_CUDA(cudaMemcpyAsync(hs.data(), stat.get(), 2 * m * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CWM_TRY(read_err(h, "amg_setup (A P)"));  // synchronises
+  const bool f32 = h->prm.vcycle_fp32 != 0;
+  for (size_t q = 0; q < m; ++q) {
+    Level &L = h->lev[todo[q]];
+    L.ap_nnz = hs[2 * q];
+    L.ap_max_row = hs[2 * q + 1];
+    CWM_TRY(L.ap_ci.alloc(L.ap_nnz, s));
+    CWM_TRY(L.ap_val.alloc(L.ap_nnz, s));
+    GalerkinWork gw;
+    gw.rpu = L.rp.get();
+    gw.ci_pad = ci_pad[q].get();
+    gw.val_pad = val_pad[q].get();
+    CWM_TRY(galerkin_compact(L.n, L.ap_rp.get(), L.ap_ci.get(), L.ap_val.get(), gw, s));
+    if (f32) {
+      CWM_TRY(L.ap_val32.alloc(L.ap_nnz, s));
+      CWM_TRY(to_float(L.ap_nnz, L.ap_val.get(), L.ap_val32.get(), s));
+    }
+  }
+  return AMG_OK;
+}
+
 amg_status finish_level(amg_hierarchy *h, Level &L) {
   cudaStream_t s = h->stream;
   {  // the long rows of a sub-warp-tile level (see long_row_min)
@@ -390,6 +498,8 @@ struct LevelVec<double> {
   static double *t1(Level &L) { return L.t1.get(); }
   static double *t2(Level &L) { return L.t2.get(); }
   static const double *dense(const Level &L) { return L.xdense.get(); }
+  static bool has_ap(const Level &L) { return L.ap_nnz > 0 && L.ap_val.get(); }
+  static CsrView<double> AP(const Level &L) { return L.ap_view<double>(L.ap_val.get()); }
 };
 template <>
 struct LevelVec<float> {
@@ -401,6 +511,8 @@ struct LevelVec<float> {
   static float *t1(Level &L) { return L.t132.get(); }
   static float *t2(Level &L) { return L.t232.get(); }
   static const float *dense(const Level &L) { return L.xdense32.get(); }
+  static bool has_ap(const Level &L) { return L.ap_nnz > 0 && L.ap_val32.get(); }
+  static CsrView<float> AP(const Level &L) { return L.ap_view<float>(L.ap_val32.get()); }
 };
 
 template <>
@@ -452,17 +564,6 @@ void fill_tail(amg_hierarchy *h, int k0, TailArgs<V> &a) {
 // x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
 template <class V>
 amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init);
-
-// Largest level whose cycle uses the fused kernels (see cycle_level), per precision.  The
-// fused forms rebuild x_j per nonzero (D^{-1} b, and D^{-1} b + P x_c), two or three FP64
-// operations per nonzero instead of one; where GB300's FP64 pipe binds, that costs more
-// than the passes saved.  3D Poisson 128^3, FP64 V-cycle: limits of 300000 / 65536 / 0 rows
-// gave 11.61 / 11.41 / 11.62 ms per solve (level 1 has 262,144 rows).
-#ifndef CWM_FUSE_MAX_ROWS64
-#define CWM_FUSE_MAX_ROWS64 65536
-#endif
-template <class V>
-constexpr int fuse_max_rows() { return sizeof(V) == 8 ? CWM_FUSE_MAX_ROWS64 : 300000; }
 
 // x^k = V-cycle(k, b^k) from x^k = 0 (Algorithm 1); b and x must not be t1/t2 of level k.
 template <class V>
@@ -522,8 +623,11 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   // sweep x = D^{-1} b is formed on the fly inside the residual and the coarse correction
   // inside the post-sweep, two kernels fewer.  On large levels the extra gathers per
   // nonzero cost more than the passes they save (measured), so they keep separate kernels;
-  // so do levels on sub-warp tiles (the fused forms exist as row-block kernels only).
-  if (zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= fuse_max_rows<V>() && A.rb) {
+  // so do levels on sub-warp tiles (the fused forms exist as row-block kernels only).  A
+  // level with A P (built for the levels that skip the fused kernels, or for every level with
+  // coupled_post = 1) takes the coarse correction and the post-sweep through it instead.
+  const bool ap = h->prm.post_sweeps == 1 && LV::has_ap(L);
+  if (!ap && zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= fuse_max_rows<V>() && A.rb) {
     CWM_TRY(resid_scaled_restrict<V>(A, C0.n, L.mptr.get(), L.mlist.get(), LV::p(L), dinv, b, t1, LV::b(C0), s));
     for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C0), LV::x(C0), g == 0));
     return prolong_jacobi<V>(A, dinv, b, L.agg.get(), LV::p(L), LV::x(C0), x, s);
@@ -540,6 +644,8 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   V *rtmp = (xs == t1) ? t2 : t1;  // free until the prolongation writes it
   CWM_TRY(resid_restrict_rb<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, rtmp, LV::b(C), s));
   for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C), LV::x(C), g == 0));
+  if (ap)  // rtmp still holds b - A xs
+    return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, rtmp, L.agg.get(), LV::p(L), LV::x(C), xs, x, s);
   V *y = (xs == t1) ? t2 : t1;
   CWM_TRY(prolong<V>(A.n, L.agg.get(), LV::p(L), LV::x(C), xs, y, s));
   const int post = h->prm.post_sweeps;
@@ -595,6 +701,7 @@ void amg_default_params(amg_params *p) {
   p->stall_ratio = 0.0;
   p->gamma = 1;
   p->galerkin_fp32_from = 0;
+  p->coupled_post = 0;
 }
 
 const char *amg_status_string(amg_status s) {
@@ -637,7 +744,8 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
     P.coarse_max = (int)lo;
   }
   if (P.sweeps_per_level < 1 || P.sweeps_per_level > kMaxSweeps || P.max_levels < 1 || P.pre_sweeps < 0 ||
-      P.post_sweeps < 0 || P.coarse_sweeps < 0 || P.coarse_max < 0 || P.galerkin_fp32_from < 0) {
+      P.post_sweeps < 0 || P.coarse_sweeps < 0 || P.coarse_max < 0 || P.galerkin_fp32_from < 0 ||
+      P.coupled_post < -1 || P.coupled_post > 1) {
     set_error("amg_setup: parameter out of range");
     return AMG_ERR_INVALID_ARG;
   }
@@ -720,6 +828,7 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
                                cudaMemcpyHostToDevice, s));
     }
   }
+  CWM_TRY(build_ap(h));
   // FCG work vectors
   CWM_TRY(h->r.alloc(n, s));
   CWM_TRY(h->w.alloc(n, s));

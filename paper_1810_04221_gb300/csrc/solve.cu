@@ -407,8 +407,11 @@ __global__ void __launch_bounds__(kRB) k_jacobi_rb(int n, const int *__restrict_
   const int nrows = min(kRB, n - r0);
   rb_stage_rp(rp, r0, nrows, sm.rp);
   const int r = r0 + threadIdx.x;
-  const V res = rb_row_dot<V, false, true>(ci, val, x, nrows, sm, threadIdx.x < nrows ? b[r] : V(0));
-  if (threadIdx.x < nrows) y[r] = fma(dinv[r], res, x[r]);
+  const bool in = threadIdx.x < nrows;
+  // the row's own operands are loaded before the row dot, so their latency overlaps it
+  const V br = in ? b[r] : V(0), dr = in ? dinv[r] : V(0), xr = in ? x[r] : V(0);
+  const V res = rb_row_dot<V, false, true>(ci, val, x, nrows, sm, br);
+  if (in) y[r] = fma(dr, res, xr);
 }
 
 template <class V>
@@ -542,6 +545,267 @@ amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const 
   CWM_TRACE("prolong", (4.0 + 4.0 * sizeof(V)) * n, s);
   CWM_CUDA(launch_pdl(k_prolong_scaled<V>, wave_cap(k_prolong_scaled<V>, grid_for(n, kBlock, num_sms() * 8), kBlock), kBlock,
                       0, s, n, agg, p, xc, dinv, b, y));
+  CWM_LAUNCH();
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------ A P ----
+// Row i of A P: for each aggregate J met among the columns j of row i, (A P)_iJ = the sum
+// of a_ij p_j over those j with agg(j) = J, added in the row's stored order.  The distinct J,
+// in order of first occurrence, go to ci_pad[rp[i] ..) with their sums in val_pad[rp[i] ..)
+// and their number in cnt[i] (at most the row's length, so the padded rows fit A's layout);
+// *maxcnt is raised to the longest row of A P.
+
+// Rows of at most MAXL entries, a thread per row: the row's list of aggregates and sums
+// stays in registers (fully unrolled, so no local memory).  Longer rows are skipped.
+template <int MAXL>
+__global__ void __launch_bounds__(kBlock)
+    k_ap_short(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ val,
+               const int *__restrict__ agg, const double *__restrict__ p, int *__restrict__ ci_pad,
+               double *__restrict__ val_pad, int *__restrict__ cnt, int *maxcnt) {
+  int dmax = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int b = rp[i], len = rp[i + 1] - b;
+    if (len > MAXL) continue;
+    int jl[MAXL];
+    double sl[MAXL];
+    int d = 0;
+#pragma unroll
+    for (int e = 0; e < MAXL; ++e) {
+      jl[e] = -1;
+      sl[e] = 0.0;
+      if (e < len) {
+        const int j = ci[b + e];
+        const int J = agg[j];
+        const double t = val[b + e] * p[j];
+        bool found = false;
+#pragma unroll
+        for (int u = 0; u < e; ++u)
+          if (u < d && jl[u] == J) { sl[u] += t; found = true; }
+#pragma unroll
+        for (int u = 0; u <= e; ++u)
+          if (!found && u == d) { jl[u] = J; sl[u] = t; }
+        d += found ? 0 : 1;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < MAXL; ++u)
+      if (u < d) { ci_pad[b + u] = jl[u]; val_pad[b + u] = sl[u]; }
+    cnt[i] = d;
+    dmax = max(dmax, d);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if ((threadIdx.x & 31) == 0 && dmax > 0) atomicMax(maxcnt, dmax);
+}
+
+// Rows longer than min_len, a warp per row: each warp reads the lengths of 32 rows at a time
+// and takes their long rows one after the other, in chunks of 32 entries.  Equal J within a
+// chunk are grouped by __match_any_sync and summed by the group's first lane, which continues
+// the sum of an aggregate already met in an earlier chunk.  The first kApHead list entries
+// (aggregate and sum) are kept in shared memory with an open-addressing index (J -> slot) and
+// written out when the row is done; later entries live in the padded row and are searched
+// there.
+constexpr int kApHead = 64;
+constexpr int kApHash = 128;  // index size (a power of two, at least twice the head)
+constexpr int kApPre = 4;     // chunks whose entries are loaded up front
+__device__ __forceinline__ int ap_hash(int J) { return (int)(((unsigned)J * 2654435761u) >> 25); }  // 7 bits
+
+__global__ void __launch_bounds__(kBlock)
+    k_ap_long(int n, int min_len, const int *__restrict__ rp, const int *__restrict__ ci,
+              const double *__restrict__ val, const int *__restrict__ agg, const double *__restrict__ p,
+              int *__restrict__ ci_pad, double *__restrict__ val_pad, int *__restrict__ cnt, int *maxcnt) {
+  __shared__ double s_t[kBlock];
+  __shared__ int s_key[kBlock / 32][kApHash];
+  __shared__ int s_slot[kBlock / 32][kApHash];
+  __shared__ int s_hj[kBlock / 32][kApHead];
+  __shared__ double s_hv[kBlock / 32][kApHead];
+  const int lane = threadIdx.x & 31;
+  const int wbase = threadIdx.x & ~31;
+  const int w = threadIdx.x >> 5;
+  int *key = s_key[w], *slot_of = s_slot[w], *hj = s_hj[w];
+  double *hv = s_hv[w];
+  const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  int dmax = 0;
+  for (long long g = warp_id * 32; g < n; g += nwarps * 32) {
+    const long long my = g + lane;
+    const int my_b = my < n ? rp[my] : 0;
+    const int my_len = my < n ? rp[my + 1] - my_b : 0;
+    unsigned todo = __ballot_sync(0xffffffffu, my_len > min_len);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const long long row = g + src;
+      const int b = __shfl_sync(0xffffffffu, my_b, src);
+      const int len = __shfl_sync(0xffffffffu, my_len, src);
+#pragma unroll
+      for (int q = 0; q < kApHash / 32; ++q) key[lane + 32 * q] = -1;
+      __syncwarp();
+      int d = 0;
+      // one chunk: entry (J, t) of this lane, has = the lane holds an entry
+      auto chunk = [&](int J, double t, bool has) {
+        s_t[threadIdx.x] = t;
+        const unsigned grp = __match_any_sync(0xffffffffu, J);
+        const bool lead = has && (__ffs(grp) - 1) == lane;
+        int pos = -1;
+        if (lead) {
+          // the index holds every head entry, at most kApHead of kApHash places: a probe
+          // meets J or an empty place
+          for (int it = 0, h = ap_hash(J); it < kApHash; ++it, h = (h + 1) & (kApHash - 1)) {
+            const int k = key[h];
+            if (k == J) { pos = slot_of[h]; break; }
+            if (k < 0) break;
+          }
+          if (pos < 0)
+            for (int u = kApHead; u < d; ++u)
+              if (ci_pad[b + u] == J) { pos = u; break; }
+        }
+        const unsigned fresh = __ballot_sync(0xffffffffu, lead && pos < 0);
+        __syncwarp();
+        if (lead) {
+          const int slot = pos < 0 ? d + __popc(fresh & ((1u << lane) - 1u)) : pos;
+          double acc = pos < 0 ? 0.0 : (slot < kApHead ? hv[slot] : val_pad[b + slot]);
+          for (unsigned q = grp; q; q &= q - 1) acc += s_t[wbase + __ffs(q) - 1];
+          if (slot < kApHead) {
+            hj[slot] = J;
+            hv[slot] = acc;
+            if (pos < 0) {  // index the new head entry (the new J of a chunk are distinct)
+              for (int it = 0, h = ap_hash(J); it < kApHash; ++it, h = (h + 1) & (kApHash - 1))
+                if (atomicCAS(&key[h], -1, J) == -1) { slot_of[h] = slot; break; }
+            }
+          } else {
+            ci_pad[b + slot] = J;
+            val_pad[b + slot] = acc;
+          }
+        }
+        d += __popc(fresh);
+        __syncwarp();  // this chunk's entries are visible to the next chunk
+      };
+      // the entries of the first kApPre chunks are loaded together: one round trip to
+      // memory for them instead of one per chunk
+      int jp[kApPre];
+      double tp[kApPre];
+#pragma unroll
+      for (int q = 0; q < kApPre; ++q) {
+        const int k = 32 * q + lane;
+        jp[q] = -1;
+        tp[q] = 0.0;
+        if (k < len) {
+          const int j = ci[b + k];
+          jp[q] = agg[j];
+          tp[q] = val[b + k] * p[j];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kApPre; ++q)
+        if (32 * q < len) chunk(jp[q], tp[q], 32 * q + lane < len);
+      for (int c = 32 * kApPre; c < len; c += 32) {
+        const bool has = c + lane < len;
+        int J = -1;
+        double t = 0.0;
+        if (has) {
+          const int j = ci[b + c + lane];
+          J = agg[j];
+          t = val[b + c + lane] * p[j];
+        }
+        chunk(J, t, has);
+      }
+      for (int u = lane; u < min(d, kApHead); u += 32) {
+        ci_pad[b + u] = hj[u];
+        val_pad[b + u] = hv[u];
+      }
+      __syncwarp();  // the head is read out before the next row resets it
+      if (lane == 0) cnt[row] = d;
+      dmax = max(dmax, d);
+    }
+  }
+  if (lane == 0 && dmax > 0) atomicMax(maxcnt, dmax);
+}
+
+amg_status ap_group(int n, long long nnz, const int *rp, const int *ci, const double *val, const int *agg,
+                    const double *p, int max_row, int *ci_pad, double *val_pad, int *cnt, int *maxcnt,
+                    cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  // A, agg and p read once, the padded rows (at most nnz entries) and the counts written
+  CWM_TRACE("ap", 4.0 * (n + 1) + 24.0 * (double)nnz + 16.0 * n, s);
+  const int grid = grid_for(n, kBlock, num_sms() * 8);
+  const int maxl = max_row <= 8 ? 8 : 16;
+  if (maxl == 8)
+    k_ap_short<8><<<grid, kBlock, 0, s>>>(n, rp, ci, val, agg, p, ci_pad, val_pad, cnt, maxcnt);
+  else
+    k_ap_short<16><<<grid, kBlock, 0, s>>>(n, rp, ci, val, agg, p, ci_pad, val_pad, cnt, maxcnt);
+  CWM_LAUNCH();
+  if (max_row > maxl) {
+    k_ap_long<<<grid_for(((long long)n + 31) / 32 * 32, kBlock, num_sms() * 8), kBlock, 0, s>>>(
+        n, maxl, rp, ci, val, agg, p, ci_pad, val_pad, cnt, maxcnt);
+    CWM_LAUNCH();
+  }
+  return AMG_OK;
+}
+
+// The coarse correction and the first post-sweep through A P:  with y = xs + P xc and
+// r = b - A xs (the residual the restriction took), b - A y = r - (A P) xc, so
+// x = y + D^{-1} (r - (A P) xc).  xs may be NULL (0).
+template <class V>
+__global__ void __launch_bounds__(kRB) k_prolong_jacobi_ap_rb(int n, const int *__restrict__ rp,
+                                                              const int *__restrict__ ci, const V *__restrict__ val,
+                                                              const V *__restrict__ dinv, const V *__restrict__ r,
+                                                              const int *__restrict__ agg, const V *__restrict__ p,
+                                                              const V *__restrict__ xc, const V *__restrict__ xs,
+                                                              V *__restrict__ x) {
+  pdl_begin();
+  __shared__ RowBlockSmem<V> sm;
+  const int r0 = blockIdx.x * kRB;
+  const int nrows = min(kRB, n - r0);
+  rb_stage_rp(rp, r0, nrows, sm.rp);
+  const int i = r0 + threadIdx.x;
+  const bool in = threadIdx.x < nrows;
+  // the row's own operands are loaded before the row dot, so their latency overlaps it
+  V ri = V(0), yi = V(0), di = V(0);
+  if (in) {
+    ri = r[i];
+    di = dinv[i];
+    yi = fma(p[i], __ldg(xc + agg[i]), xs ? xs[i] : V(0));
+  }
+  const V res = rb_row_dot<V, false, true>(ci, val, xc, nrows, sm, ri);
+  if (in) x[i] = fma(di, res, yi);
+}
+
+template <class V, int T>
+__global__ void __launch_bounds__(kBlock)
+    k_prolong_jacobi_ap(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ val,
+                        const V *__restrict__ dinv, const V *__restrict__ r, const int *__restrict__ agg,
+                        const V *__restrict__ p, const V *__restrict__ xc, const V *__restrict__ xs,
+                        V *__restrict__ x) {
+  pdl_begin();
+  CWM_TILE_LOOP(T, n) {
+    const long long row = base + sub;
+    const bool active = row < n;
+    V ri = V(0), yi = V(0), di = V(0);
+    if (active && lane == 0) {
+      ri = r[row];
+      di = dinv[row];
+      yi = fma(p[row], __ldg(xc + agg[row]), xs ? xs[row] : V(0));
+    }
+    const V res = tile_row_dot<V, T, true>(rp, ci, val, xc, row, active, lane, ri);
+    if (active && lane == 0) x[row] = fma(di, res, yi);
+  }
+}
+
+template <class V>
+amg_status prolong_jacobi_ap(const CsrView<V> &AP, int nc, const V *dinv, const V *r, const int *agg, const V *p,
+                             const V *xc, const V *xs, V *x, cudaStream_t s) {
+  if (AP.n == 0) return AMG_OK;
+  CWM_TRACE("prolong_jacobi", 4.0 * (AP.n + 1) + (4.0 + sizeof(V)) * AP.nnz +
+                                  ((xs ? 5.0 : 4.0) * sizeof(V) + 4.0) * AP.n + sizeof(V) * (double)nc, s);
+  if (AP.rb) {
+    CWM_CUDA(launch_pdl(k_prolong_jacobi_ap_rb<V>, rb_grid(AP.n), kRB, 0, s, AP.n, AP.rp, AP.ci, AP.val, dinv, r, agg, p,
+                        xc, xs, x));
+  } else {
+    CWM_DISPATCH_T(AP.tile, CWM_CUDA(launch_pdl(k_prolong_jacobi_ap<V, kT>, rows_grid(AP.n, kT), kBlock, 0, s, AP.n, AP.rp,
+                                                AP.ci, AP.val, dinv, r, agg, p, xc, xs, x)));
+  }
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -1258,6 +1522,8 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
                                         const V *, V *, cudaStream_t);                                       \
   template amg_status prolong_scaled<V>(int, const int *, const V *, const V *, const V *, const V *, V *,    \
                                         cudaStream_t);                                                       \
+  template amg_status prolong_jacobi_ap<V>(const CsrView<V> &, int, const V *, const V *, const int *, const V *, \
+                                           const V *, const V *, V *, cudaStream_t);                          \
   template amg_status add_to<V>(int, const V *, V *, cudaStream_t);
 CWM_INST(double)
 CWM_INST(float)

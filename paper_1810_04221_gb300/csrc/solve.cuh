@@ -81,6 +81,19 @@ amg_status prolong_jacobi(const CsrView<V> &A, const V *dinv, const V *b, const 
 template <class V>
 amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const V *dinv, const V *b, V *y,
                           cudaStream_t s);
+// Row i of A P (P: one entry p_i in column agg_i per row) into A's padded layout: the
+// distinct aggregates J of row i's columns, in order of first occurrence, at ci_pad[rp[i] ..),
+// (A P)_iJ = sum of a_ij p_j in the row's order at val_pad[rp[i] ..), their number at cnt[i];
+// *maxcnt (zeroed by the caller) is raised to the longest row of A P.  max_row: the
+// longest row of A.
+amg_status ap_group(int n, long long nnz, const int *rp, const int *ci, const double *val, const int *agg,
+                    const double *p, int max_row, int *ci_pad, double *val_pad, int *cnt, int *maxcnt,
+                    cudaStream_t s);
+// x = y + D^{-1} (r - (A P) xc) with y = xs + P xc and r = b - A xs: the coarse correction
+// and one post-sweep (xs may be NULL: 0); AP: the stored product A P, nc: columns of P
+template <class V>
+amg_status prolong_jacobi_ap(const CsrView<V> &AP, int nc, const V *dinv, const V *r, const int *agg, const V *p,
+                             const V *xc, const V *xs, V *x, cudaStream_t s);
 // r = b - A x (any value type)
 template <class V>
 amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s);

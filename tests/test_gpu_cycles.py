@@ -102,6 +102,74 @@ def test_long_row_split_hierarchy(fp32):
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
 
 
+COUPLED_CASES = CASES + [
+    # level 0 (110,592 rows) is above the FP64 fused-kernel limit: the unfused cycle
+    ("poisson3d_48_s3", lambda: P.poisson3d(48), 3, 100),
+    # hub rows of ~300 entries meeting more than 64 distinct aggregates: the warp grouping's
+    # search beyond its register copy of the list
+    ("hubs_s2", lambda: P.random_spd_hubs(6000, 5.0, n_hubs=8, hub_degree=300, seed=5), 2, 40),
+]
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("coupled", [-1, 0, 1])
+@pytest.mark.parametrize("case", COUPLED_CASES, ids=[c[0] for c in COUPLED_CASES])
+def test_vcycle_coupled_post(case, coupled, fp32):
+    """Coarse correction + post-sweep as one pass over the stored A P: with y = xs + P xc,
+    b - A y = (b - A xs) - (A P) xc, an identity of the V-cycle of Algorithm 1; the result
+    matches the oracle's literal cycle.  coupled_post = 1 takes it on every level below the
+    coarsest, 0 on long-row levels outside the fused small-level kernels, -1 never."""
+    name, gen, sweeps, cmax = case
+    mat = gen()
+    n = len(mat[0]) - 1
+    v = np.ones(n)
+    H = oracle.Hierarchy(*mat, v, sweeps=sweeps, coarse_max=cmax)
+    prm = B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, coupled_post=coupled, vcycle_fp32=fp32)
+    h = B.amg_setup(*csr_dev(*mat), dev(v), prm)
+    try:
+        B.amg_trace_enable(h, True)
+        r = np.random.default_rng(7).standard_normal(n)
+        w = torch.empty(n, dtype=torch.float64, device="cuda")
+        got = host(B.amg_vcycle(h, dev(r), w))
+        names = {e["name"] for e in B.amg_trace(h)}
+    finally:
+        h.free()
+    ref = H.vcycle(r)
+    assert np.abs(got - ref).max() <= (2e-5 if fp32 else 1e-12) * np.abs(ref).max()
+    # level 0 through A P: a pre-sweep `scale` and no separate post-sweep `jacobi`
+    used = "scale@0" in names and "jacobi@0" not in names
+    if name.startswith("poisson3d"):  # 7-entry rows: auto mode leaves them to the separate passes
+        assert used == (coupled == 1)
+    if name.startswith("elasticity"):  # 81-entry rows on sub-warp tiles: auto builds A P
+        assert used == (coupled >= 0)
+
+
+@pytest.mark.parametrize("coupled", [-1, 1])
+def test_pcg_and_wcycle_coupled_post(coupled):
+    """FCG iterations and solution with the A P post-sweep on every level, V- and W-cycle."""
+    mat = P.poisson3d(24)
+    n = len(mat[0]) - 1
+    v = np.ones(n)
+    xs, b = P.manufactured_rhs(*mat, seed=8)
+    for gamma in (1, 2):
+        H = oracle.Hierarchy(*mat, v, sweeps=3, coarse_max=20, gamma=gamma)
+        xr, st_r, it_r, _, _ = H.pcg(b, rtol=1e-8, itmax=300)
+        h = B.amg_setup(*csr_dev(*mat), dev(v), B.amg_default_params(sweeps_per_level=3, coarse_max=20, gamma=gamma,
+                                                                    coupled_post=coupled))
+        try:
+            r = np.random.default_rng(3).standard_normal(n)
+            w = torch.empty(n, dtype=torch.float64, device="cuda")
+            ref = H.vcycle(r)
+            assert np.abs(host(B.amg_vcycle(h, dev(r), w)) - ref).max() <= 1e-12 * np.abs(ref).max()
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8, itmax=300)
+        finally:
+            h.free()
+        assert st == B.AMG_OK and st_r == oracle.OK
+        assert it_r - 1 <= info["iters"] <= it_r + 1
+        assert np.abs(host(x) - xr).max() <= 1e-7 * np.abs(xr).max()
+
+
 @pytest.mark.parametrize("tail_rows", [-1, 0])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_vcycle_fp32(case, tail_rows):
