@@ -1240,15 +1240,17 @@ __global__ void __launch_bounds__(kRB)
   // block-wide FP64 reduction is paid once per block, not once per 256 rows
   for (int r0 = blockIdx.x * kRB; r0 < n; r0 += gridDim.x * kRB) {
     const int nrows = min(kRB, n - r0);
+    const int i = r0 + threadIdx.x;
+    const bool in = threadIdx.x < nrows;
+    // the row's own w_i, r_i, q_i are loaded before the row dot, so their latency overlaps it
+    const double wi = in ? w[i] : 0.0, ri = in ? r[i] : 0.0, qi = (in && q) ? q[i] : 0.0;
     rb_stage_rp(rp, r0, nrows, sm.rp);
     const double dot = rb_row_dot<double, false>(ci, val, w, nrows, sm);
-    const int i = r0 + threadIdx.x;
-    if (threadIdx.x < nrows) {
+    if (in) {
       v[i] = dot;
-      const double wi = w[i];
-      sa = fma(wi, r[i], sa);
+      sa = fma(wi, ri, sa);
       sb = fma(wi, dot, sb);
-      if (q) sg = fma(wi, q[i], sg);
+      if (q) sg = fma(wi, qi, sg);
     }
   }
   const double in3[3] = {sa, sb, sg};

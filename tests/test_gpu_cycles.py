@@ -67,6 +67,15 @@ def test_vcycle_sweep_counts(pre, post, tail_rows):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("pre", [0, 2])
+def test_vcycle_sweep_counts_coupled(pre):
+    """The A P post-sweep after zero or two pre-sweeps (the residual the restriction formed
+    is b - A xs with xs = 0 or two sweeps); two post-sweeps keep the separate passes."""
+    for post in (1, 2):
+        got, ref = _vcycle_pair(P.poisson3d(20), 3, 20, dict(tail_rows=-1, coupled_post=1), pre=pre, post=post)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_coarsest_above_dense_limit():
     """A coarsest level larger than the dense-operator limit (2048 rows) runs its sweeps."""
     mat = P.poisson2d(80)  # 6400 rows; coarse_max large keeps it a single level

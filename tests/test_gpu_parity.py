@@ -333,6 +333,12 @@ def test_rejects_bad_inputs():
     with pytest.raises(B.AmgError) as e:
         B.amg_setup(*csr_dev(rp, np.array([0, 1, 0, 1], np.int32), np.array([2.0, -1.0, -0.5, 2.0])), dev(np.ones(2)))
     assert e.value.status == B.AMG_ERR_INVALID_ARG
+    # parameters out of range
+    mat = P.poisson2d(4)
+    for bad in (dict(coupled_post=2), dict(coupled_post=-2), dict(pre_sweeps=-1), dict(sweeps_per_level=0)):
+        with pytest.raises(B.AmgError) as e:
+            B.amg_setup(*csr_dev(*mat), dev(np.ones(16)), B.amg_default_params(**bad))
+        assert e.value.status == B.AMG_ERR_INVALID_ARG
     # an aggregate with three members
     with pytest.raises(B.AmgError) as e:
         mat = P.poisson2d(4)
