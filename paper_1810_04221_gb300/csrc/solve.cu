@@ -433,34 +433,6 @@ amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V 
 }
 
 // ------------------------------------------------------------ residual + restriction ----
-// One tile per coarse row I; its members' residual rows are formed in turn and
-// accumulated in member order (ascending), so the result is deterministic.
-template <class V, int T>
-__global__ void __launch_bounds__(kBlock)
-    k_resid_restrict(int nc, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ val,
-                     const int *__restrict__ mptr, const int *__restrict__ mlist, const V *__restrict__ p,
-                     const V *__restrict__ b, const V *__restrict__ x, V *__restrict__ bc) {
-  pdl_begin();
-  CWM_TILE_LOOP(T, nc) {
-    const long long I = base + sub;
-    const bool active = I < nc;
-    int ms = 0, me = 0;
-    if (active) { ms = mptr[I]; me = mptr[I + 1]; }
-    // members per tile differ: loop to the warp's maximum so the shuffles stay uniform
-    int cnt = me - ms, cmax = cnt;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-    V acc = V(0);
-    for (int t = 0; t < cmax; ++t) {
-      const bool has = t < cnt;
-      const int m = has ? mlist[ms + t] : 0;
-      const V dot = tile_row_dot<V, T>(rp, ci, val, x, m, has, lane);
-      if (has) acc += p[m] * (b[m] - dot);
-    }
-    if (active && lane == 0) bc[I] = acc;
-  }
-}
-
 template <class V>
 __global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__restrict__ mlist,
                            const V *__restrict__ p, const V *__restrict__ r, V *__restrict__ bc);
@@ -504,15 +476,6 @@ __global__ void __launch_bounds__(kRB) k_prolong_jacobi_rb(int n, const int *__r
   }
 }
 
-// y = D^{-1} b + P xc
-template <class V>
-__global__ void k_prolong_scaled(int n, const int *__restrict__ agg, const V *__restrict__ p, const V *__restrict__ xc,
-                                 const V *__restrict__ dinv, const V *__restrict__ b, V *__restrict__ y) {
-  pdl_begin();
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = fma(p[i], __ldg(xc + agg[i]), dinv[i] * b[i]);
-}
-
 template <class V>
 amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                                  const V *dinv, const V *b, V *r_scratch, V *bc, cudaStream_t s) {
@@ -534,17 +497,6 @@ amg_status prolong_jacobi(const CsrView<V> &A, const V *dinv, const V *b, const 
   if (A.n == 0) return AMG_OK;
   CWM_TRACE("prolong_jacobi", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + (5.0 * sizeof(V) + 4.0) * A.n, s);
   CWM_CUDA(launch_pdl(k_prolong_jacobi_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, agg, p, xc, x));
-  CWM_LAUNCH();
-  return AMG_OK;
-}
-
-template <class V>
-amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const V *dinv, const V *b, V *y,
-                          cudaStream_t s) {
-  if (n == 0) return AMG_OK;
-  CWM_TRACE("prolong", (4.0 + 4.0 * sizeof(V)) * n, s);
-  CWM_CUDA(launch_pdl(k_prolong_scaled<V>, wave_cap(k_prolong_scaled<V>, grid_for(n, kBlock, num_sms() * 8), kBlock), kBlock,
-                      0, s, n, agg, p, xc, dinv, b, y));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -903,19 +855,6 @@ amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const
   }
   CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
   CWM_CUDA(launch_pdl(k_restrict<V>, grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s, nc, mptr, mlist, p, r_scratch, bc));
-  CWM_LAUNCH();
-  return AMG_OK;
-}
-
-template <class V>
-amg_status resid_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
-                          const V *b, const V *x, V *bc, cudaStream_t s) {
-  if (nc == 0) return AMG_OK;
-  CWM_TRACE("resid_restrict", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + (3.0 * sizeof(V) + 4.0) * A.n +
-                                  (4.0 + sizeof(V)) * nc, s);
-  CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_resid_restrict<V, kT>, wave_cap(k_resid_restrict<V, kT>, rows_grid(nc, kT), kBlock),
-                                             kBlock, 0, s, nc, A.rp, A.ci, A.val, mptr,
-                                                                                      mlist, p, b, x, bc)));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -1337,44 +1276,6 @@ amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const do
   return AMG_OK;
 }
 
-__global__ void k_fcg_scalars(int nb, const double *__restrict__ part, double *scal, int first) {
-  double a = 0.0, b = 0.0, g = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    a += part[3 * i];
-    b += part[3 * i + 1];
-    g += part[3 * i + 2];
-  }
-  a = block_sum(a);
-  b = block_sum(b);
-  g = block_sum(g);
-  if (threadIdx.x == 0) {
-    double rho, coef;
-    if (first) {
-      rho = b;
-      coef = 0.0;
-      g = 0.0;
-    } else {
-      const double rp = scal[kRhoPrev];
-      rho = b - g * g / rp;
-      coef = g / rp;
-    }
-    scal[kAlpha] = a;
-    scal[kBeta] = b;
-    scal[kGamma] = g;
-    scal[kRho] = rho;
-    scal[kCoef] = coef;
-    scal[kStep] = a / rho;
-    scal[kRhoPrev] = rho;
-    if (!(rho > 0.0) || !isfinite(rho) || !isfinite(a)) scal[kFlags] = 1.0;
-  }
-}
-
-amg_status fcg_scalars(int nb, const double *part, double *scal, int first, cudaStream_t s) {
-  k_fcg_scalars<<<1, 1024, 0, s>>>(nb, part, scal, first);
-  CWM_LAUNCH();
-  return AMG_OK;
-}
-
 // The two pairs of AXPYs of Algorithm 3, each first result reused from registers:
 // d = w - coef d, x += step d;  q = v - coef q, r -= step q;  then partial r.r.
 __global__ void __launch_bounds__(kBlock)
@@ -1510,8 +1411,6 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
 #define CWM_INST(V)                                                                                          \
   template amg_status scale<V>(int, const V *, const V *, V *, cudaStream_t);                                \
   template amg_status jacobi<V>(const CsrView<V> &, const V *, const V *, const V *, V *, cudaStream_t);     \
-  template amg_status resid_restrict<V>(const CsrView<V> &, int, const int *, const int *, const V *,        \
-                                        const V *, const V *, V *, cudaStream_t);                            \
   template amg_status prolong<V>(int, const int *, const V *, const V *, const V *, V *, cudaStream_t);      \
   template amg_status resid_restrict_rb<V>(const CsrView<V> &, int, const int *, const int *, const V *,     \
                                            const V *, const V *, V *, V *, cudaStream_t);                    \
@@ -1522,8 +1421,6 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
                                                const V *, const V *, V *, V *, cudaStream_t);               \
   template amg_status prolong_jacobi<V>(const CsrView<V> &, const V *, const V *, const int *, const V *,    \
                                         const V *, V *, cudaStream_t);                                       \
-  template amg_status prolong_scaled<V>(int, const int *, const V *, const V *, const V *, const V *, V *,    \
-                                        cudaStream_t);                                                       \
   template amg_status prolong_jacobi_ap<V>(const CsrView<V> &, int, const V *, const V *, const int *, const V *, \
                                            const V *, const V *, V *, cudaStream_t);                          \
   template amg_status add_to<V>(int, const V *, V *, cudaStream_t);

@@ -53,10 +53,6 @@ amg_status scale(int n, const V *dinv, const V *b, V *y, cudaStream_t s);
 // y = x + dinv .* (b - A x)   (x, y distinct)
 template <class V>
 amg_status jacobi(const CsrView<V> &A, const V *dinv, const V *b, const V *x, V *y, cudaStream_t s);
-// bc[I] = sum_{m in I} p_m (b_m - (A x)_m), members mlist[mptr[I] .. mptr[I+1]); x may be NULL (0)
-template <class V>
-amg_status resid_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
-                          const V *b, const V *x, V *bc, cudaStream_t s);
 // Largest coarsest level whose sweeps are turned into a dense operator at setup.
 constexpr int kDenseCoarseMax = 2048;
 // X (n*n, row-major) = the linear map of `sweeps` l1-Jacobi sweeps from zero; tmp: n*n
@@ -77,10 +73,6 @@ amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, c
 template <class V>
 amg_status prolong_jacobi(const CsrView<V> &A, const V *dinv, const V *b, const int *agg, const V *p, const V *xc,
                           V *x, cudaStream_t s);
-// y = D^{-1} b + P xc
-template <class V>
-amg_status prolong_scaled(int n, const int *agg, const V *p, const V *xc, const V *dinv, const V *b, V *y,
-                          cudaStream_t s);
 // Row i of A P (P: one entry p_i in column agg_i per row) into A's padded layout: the
 // distinct aggregates J of row i's columns, in order of first occurrence, at ci_pad[rp[i] ..),
 // (A P)_iJ = sum of a_ij p_j in the row's order at val_pad[rp[i] ..), their number at cnt[i];
@@ -150,8 +142,6 @@ int fcg_update_blocks(int n);    // partial sums written by fcg_update
 // and step = alpha/rho in scal (tick: a zeroed counter, left zeroed)
 amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const double *r, const double *q,
                              double *v, double *part, double *scal, unsigned *tick, int first, cudaStream_t s);
-// scalars from the partials: alpha, beta, gamma, rho, coef = gamma/rho_prev, step = alpha/rho
-amg_status fcg_scalars(int nb, const double *part, double *scal, int first, cudaStream_t s);
 // d = w - coef d; q = v - coef q; x += step d; r -= step q; r.r into scal[kRR] (last block)
 amg_status fcg_update(int n, const double *w, const double *v, double *d, double *q, double *x, double *r,
                       double *scal, double *part, unsigned *tick, int first, cudaStream_t s);
