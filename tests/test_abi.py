@@ -52,6 +52,9 @@ def test_library_loads_and_host_calls_work(lib_path):
     p = binding.amg_default_params()
     assert (p.sweeps_per_level, p.coarse_max, p.max_levels) == (2, 40, 40)
     assert (p.pre_sweeps, p.post_sweeps, p.coarse_sweeps) == (1, 1, 20)
+    # the remaining documented defaults
+    assert (p.vcycle_fp32, p.check_input, p.keep_sweeps, p.loop_cap, p.trace) == (0, 1, 0, 0, 0)
+    assert (p.tail_rows, p.stall_ratio, p.gamma, p.galerkin_fp32_from, p.coupled_post) == (-1, 0.0, 1, 0, 0)
     assert binding.status_name(binding.AMG_ERR_NOT_SPD) == "AMG_ERR_NOT_SPD"
     # argument checks happen before any device work
     lib.amg_num_levels.restype = C.c_int
@@ -59,14 +62,22 @@ def test_library_loads_and_host_calls_work(lib_path):
 
 
 def test_struct_layout_matches_c(tmp_path):
-    """sizeof/offsetof of the public structs, compiled by the host C compiler."""
+    """sizeof and every field's offsetof of the public structs, compiled by the host C
+    compiler, against the ctypes mirrors."""
     from paper_1810_04221_gb300 import binding
+    structs = [("amg_params", binding.AmgParams), ("amg_info", binding.AmgInfo)]
+    lines = []
+    for cname, cls in structs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        lines += [f'printf("%zu\\n", offsetof({cname}, {f}));' for f, _ in cls._fields_]
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cwm_amg.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(amg_params), offsetof(amg_params, loop_cap),'
-                   ' sizeof(amg_info), offsetof(amg_info, t_solve_ms));return 0;}\n')
+                   'int main(void){' + "".join(lines) + 'return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", B.INCLUDE, str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
-    assert got == [C.sizeof(binding.AmgParams), binding.AmgParams.loop_cap.offset,
-                   C.sizeof(binding.AmgInfo), binding.AmgInfo.t_solve_ms.offset]
+    want = []
+    for _, cls in structs:
+        want.append(C.sizeof(cls))
+        want += [getattr(cls, f).offset for f, _ in cls._fields_]
+    assert got == want
