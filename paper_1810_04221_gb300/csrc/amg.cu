@@ -359,8 +359,8 @@ constexpr int fuse_max_rows() { return sizeof(V) == 8 ? CWM_FUSE_MAX_ROWS64 : 30
 constexpr int kApMaxRow = 1024;
 
 // In auto mode A P is built for levels whose mean row is longer than this.  Measured on
-// GB300 (setup + one solve): Q1 elasticity 64^3 (78 entries per row, A P about a third of
-// that) 71.4 -> 68.8 ms; on the 7-entry rows of 3D Poisson 128^3 and the lognormal 160^3
+// GB300 (setup + one solve): Q1 elasticity 64^3 (64 entries per row, A P a little over half
+// of them) 71.4 -> 68.8 ms; on the 7-entry rows of 3D Poisson 128^3 and the lognormal 160^3
 // levels the solve gained what building A P cost (FP64 17.98 -> 18.01 ms, FP32 16.18 ->
 // 16.24 ms, lognormal 44.9 -> 45.5 ms), so short-row levels keep the separate passes.
 constexpr double kApAutoMinMean = 16.0;
