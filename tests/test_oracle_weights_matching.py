@@ -194,6 +194,33 @@ def test_greedy_equals_sequential_suitor(seed, ties):
     _check_greedy_characterisation(rp, ci, w, m1)
 
 
+def _python_greedy(edges, n, key):
+    """Textbook greedy matching: scan the edges in decreasing key, take an edge whose ends
+    are both free."""
+    mate = [-1] * n
+    for (a, b) in sorted(edges, key=lambda e: key(edges[e], e[0], e[1]), reverse=True):
+        if mate[a] < 0 and mate[b] < 0:
+            mate[a], mate[b] = b, a
+    return np.array(mate)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_equals_python_greedy_with_ties(seed):
+    """The oracle's matching equals a plain Python greedy under the key (c, b, a).  Ties are
+    frequent here (weights from two values); the key compared as (c, a, b) gives the same
+    matching too: at a shared vertex both orders compare the other endpoint, and the greedy
+    result depends only on how adjacent edges compare."""
+    rp, ci, val = P.random_spd(300, 6.0, seed=40 + seed, ties=True)
+    w = oracle.edge_weights(rp, ci, val, np.ones(300))
+    edges = _edges(rp, ci, w)
+    assert len(set(edges.values())) < len(edges) // 4  # many ties
+    got = oracle.greedy_match(rp, ci, w)
+    assert np.array_equal(got, _python_greedy(edges, 300, lambda c, a, b: (c, b, a)))
+    assert np.array_equal(got, _python_greedy(edges, 300, lambda c, a, b: (c, a, b)))
+    # the reverse tie-break (smaller endpoints first) is a different matching
+    assert not np.array_equal(got, _python_greedy(edges, 300, lambda c, a, b: (c, -b, -a)))
+
+
 def test_matching_poisson2d_closed_form():
     # all weights tie at 1.25; under the (c, b, a) order greedy pairs {2m, 2m+1} in every row
     m = 64
