@@ -135,6 +135,14 @@ def elasticity_q1(nodes: int = 64, E: float = 1.0, nu: float = 0.3):
 
     The clamped dofs are eliminated (not kept as identity rows).  Unknowns are
     dof-interleaved: 3 * node + component over the free nodes in (z, y, x) order.
+
+    The stored pattern is the assembled one: every (dof, dof) pair of two nodes that share
+    an element, 9 entries per such node pair (27 node neighbours inside the grid), whether
+    or not the assembled sum is exactly zero.  With nodes = 64 that is n = 774,144 and
+    nnz = 9 * 187 * 190^2 = 60,756,300 (about 78.5 per row); some 11.5M of them are exact
+    zeros of the assembly (couplings that cancel between the elements around an edge or a
+    face), kept as stored zeros.  The nonzero values are the element sums, made exactly
+    symmetric as 0.5 (K + K^T).
     """
     ne = nodes - 1
     h = 1.0 / ne
@@ -153,7 +161,6 @@ def elasticity_q1(nodes: int = 64, E: float = 1.0, nu: float = 0.3):
     new_node[free_node] = np.arange(int(free_node.sum()))
     dof_map = (3 * new_node[:, None] + np.arange(3)[None, :]).ravel()
     dof_map[np.repeat(~free_node, 3)] = -1
-    nfree = 3 * int(free_node.sum())
     K = sp.csr_matrix((ndof, ndof))
     # assemble in chunks of elements to bound memory
     chunk = 65536
@@ -165,8 +172,45 @@ def elasticity_q1(nodes: int = 64, E: float = 1.0, nu: float = 0.3):
         K = K + sp.coo_matrix((v, (r, c)), shape=(ndof, ndof)).tocsr()
     keep = np.flatnonzero(dof_map >= 0)
     K = K[keep][:, keep]
-    K = 0.5 * (K + K.T)  # exact symmetry after floating-point assembly
-    return _to_csr(K)
+    K = sp.csr_matrix(0.5 * (K + K.T))  # exact symmetry after floating-point assembly
+    K.sort_indices()
+    return _q1_pattern_with_values(nodes, K)
+
+
+def _q1_pattern_with_values(nodes: int, K: sp.csr_matrix):
+    """The clamped Q1 pattern (free nodes x = 1..nodes-1, y, z = 0..nodes-1; a node couples
+    to the 27 nodes around it) in CSR with ascending columns, values looked up in K (which
+    holds only the nonzero sums); every entry of K must lie in the pattern."""
+    X, Y, Z = nodes - 1, nodes, nodes
+    nn = X * Y * Z
+    z, y, x = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    z, y, x = z.ravel(), y.ravel(), x.ravel()
+    offs = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    valid = np.empty((nn, 27), bool)
+    cnode = np.empty((nn, 27), np.int64)
+    for o, (dz, dy, dx) in enumerate(offs):  # lexicographic (dz, dy, dx): ascending columns
+        valid[:, o] = ((0 <= z + dz) & (z + dz < Z) & (0 <= y + dy) & (y + dy < Y)
+                       & (0 <= x + dx) & (x + dx < X))
+        cnode[:, o] = np.arange(nn) + (dz * Y + dy) * X + dx
+    cols = 3 * cnode[:, :, None] + np.arange(3)[None, None, :]              # (nn, 27, 3)
+    ci = np.broadcast_to(cols[:, None], (nn, 3, 27, 3))[
+        np.broadcast_to(valid[:, None, :, None], (nn, 3, 27, 3))].astype(np.int64)
+    lens = np.repeat(3 * valid.sum(axis=1), 3)
+    n = 3 * nn
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    rows = np.repeat(np.arange(n, dtype=np.int64), lens)
+    key = rows * n + ci
+    del rows
+    kr = np.repeat(np.arange(n, dtype=np.int64), np.diff(K.indptr))
+    kkey = kr * n + K.indices.astype(np.int64)
+    del kr
+    pos = np.searchsorted(key, kkey)
+    if not (pos < len(key)).all() or not np.array_equal(key[np.minimum(pos, len(key) - 1)], kkey):
+        raise AssertionError("assembled entry outside the Q1 node-neighbour pattern")
+    val = np.zeros(len(key), np.float64)
+    val[pos] = K.data
+    return rp.astype(np.int32), ci.astype(np.int32), val
 
 
 def _exact_csr(n: int, r: np.ndarray, c: np.ndarray, v: np.ndarray):

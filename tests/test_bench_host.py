@@ -74,3 +74,37 @@ def test_committed_traffic_entries_are_well_formed():
         assert len(e["source_sha256"]) == 64 and e["dram_bytes_per_launch"] > 0
         with open(f"{bench.ROOT}/{e['profile']}") as p:
             assert e["kernel"] in p.read()
+
+
+def test_elasticity_workload_shape():
+    """The default workload: Q1 elasticity on 64^3 nodes with the x = 0 face eliminated,
+    the assembled pattern's stored zeros included, body force b ~ U[-1, 1]."""
+    _, mat, v, b, xs, sweeps, cmax, fp32, extra = bench.workload("elasticity_64")
+    n = 3 * 63 * 64 ** 2
+    assert len(mat[0]) - 1 == n == 774144 and len(mat[1]) == 60756300
+    assert (sweeps, cmax, fp32, extra) == (2, 1000, True, {})
+    assert xs is None and b.shape == (n,) and np.abs(b).max() <= 1.0
+    assert np.array_equal(b, np.random.default_rng(0).uniform(-1.0, 1.0, size=n))
+    c = v[:3]
+    assert np.array_equal(v, np.tile(c, n // 3)) and (0.5 <= c).all() and (c <= 1.5).all()
+
+
+def test_cpu_samples_are_coarser_instances():
+    """Every workload's CPU sample is a workload of the same family with no more entries."""
+    for name, sample in bench.CPU_SAMPLE.items():
+        assert name.split("_")[0] == sample.split("_")[0]
+        assert int(sample.split("_")[1]) <= int(name.split("_")[1])
+
+
+def test_both_arms_share_the_config_keys():
+    a = bench.bench_config("elasticity_64", 10, 20, "d", 2, 1000, 1e-8, True, 1)
+    assert set(a) == {"workload", "desc", "n", "nnz", "sweeps_per_level", "coarse_max", "rtol", "vcycle_fp32",
+                      "l2", "parallelism"}
+
+
+def test_class_rooflines():
+    tr = [{"name": "spmv_dots", "launches": 2, "total_ms": 0.2, "bytes": 1.0e9},
+          {"name": "weights", "launches": 0, "total_ms": 0.0, "bytes": 0.0}]
+    out = bench.class_rooflines(tr, 5000.0)
+    assert len(out) == 1 and out[0]["avg_launch_us"] == 100.0
+    assert out[0]["achieved_gbs"] == 5000.0 and out[0]["frac"] == 1.0

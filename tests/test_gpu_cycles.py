@@ -3,8 +3,8 @@ pre/post sweep counts, and the float32 V-cycle inside the float64 FCG.
 
 Tolerances: float64 V-cycle 1e-12 relative (summation order differs from the oracle's);
 float32 V-cycle 2e-5 relative to the float64 oracle (unit roundoff 6e-8 times the
-work per row and the levels); FCG with the float32 V-cycle must still reach 1e-8 with at
-most three more iterations than the oracle's float64 run.
+work per row and the levels); FCG with the float32 V-cycle must still reach 1e-8 within
+one iteration of the oracle's float64 run.
 """
 import numpy as np
 import pytest
@@ -202,7 +202,7 @@ def test_pcg_fp32_vcycle(case):
     st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8, itmax=500)
     h.free()
     assert st == B.AMG_OK and st_r == oracle.OK
-    assert it_r - 1 <= info["iters"] <= it_r + 3
+    assert abs(info["iters"] - it_r) <= 1
     assert info["rel_res_true"] <= 2e-8
     assert np.abs(host(x) - xr).max() <= 1e-6 * np.abs(xr).max()
 
@@ -247,6 +247,6 @@ def test_wcycle_matches_oracle(gen, sweeps, cmax, fp32):
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8, itmax=300)
         assert st == B.AMG_OK and st_r == oracle.OK
-        assert it_r - 1 <= info["iters"] <= it_r + (3 if fp32 else 1)
+        assert abs(info["iters"] - it_r) <= 1
     finally:
         h.free()

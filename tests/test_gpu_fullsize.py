@@ -71,7 +71,7 @@ def test_poisson128_solve_vs_oracle(B, problem, fp32):
     st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8)
     h.free()
     assert st == B.AMG_OK and st_r == oracle.OK
-    assert abs(info["iters"] - it_r) <= (1 if not fp32 else 3)
+    assert abs(info["iters"] - it_r) <= 1
     assert info["rel_res_true"] <= 2e-8
     xg = host(x)
     assert np.abs(xg - xr).max() <= 1e-6 * np.abs(xr).max()

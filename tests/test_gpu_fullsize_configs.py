@@ -1,13 +1,14 @@
 """GPU: the other benchmark configurations at full size, against the oracle run at the
 same size -- 3D lognormal FV diffusion 160^3 (log-kappa N(0, 2^2), 3 sweeps per level,
 coarse n <= 1000, stall ratio 1.2) and Q1 elasticity on 64^3 nodes (2 sweeps per level,
-coarse n <= 1000), in the launch configuration bench.py times (FP64 setup, FP32 V-cycle in
+coarse n <= 1000; the assembled pattern with its stored zeros, 60,756,300 entries), in the
+launch configuration bench.py times (FP64 setup, FP32 V-cycle in
 FP64 FCG).
 
 Every level of the hierarchy is compared bit for bit (SHA-256 digests of the CSR arrays,
 smooth vectors, aggregates and prolongator values); the FCG with the FP32 V-cycle must
-reach 1e-8 within three iterations of the oracle's FP64 run and agree with its solution to
-1e-6 relative.  The two oracle runs (about a minute each) go to spawned worker processes
+reach 1e-8 within one iteration of the oracle's FP64 run and agree with its solution to
+1e-6 relative.  The two oracle runs (one to three minutes each) go to spawned worker processes
 when the module starts.
 """
 import concurrent.futures as cf
@@ -65,7 +66,7 @@ def test_fullsize_config_vs_oracle(B, oracle_runs, workload):
     for k, (g, r) in enumerate(zip(got, ref["levels"])):
         assert g == tuple(r), f"level {k} differs"
     assert st == B.AMG_OK and ref["status"] == 0
-    assert abs(info["iters"] - ref["iters"]) <= 3
+    assert abs(info["iters"] - ref["iters"]) <= 1
     assert info["rel_res_true"] <= 2e-8
     xr = ref["x"]
     assert np.abs(host(x) - xr).max() <= 1e-6 * np.abs(xr).max()

@@ -121,7 +121,7 @@ def test_hierarchy_fp32_galerkin_bit_exact(case, from_level):
 @pytest.mark.parametrize("vfp32", [0, 1])
 def test_pcg_fp32_galerkin_vs_float64_oracle(vfp32):
     """Lognormal diffusion 24^3: FCG on the binary32-Galerkin hierarchy takes the oracle's
-    iterations on the same hierarchy (within one, three with the float32 V-cycle) and at
+    iterations on the same hierarchy (within one, either V-cycle precision) and at
     most two more than on the float64 hierarchy; the coarse operators differ from the
     float64 ones by float rounding where the patterns coincide."""
     mat = P.lognormal_diffusion(24, seed=4)
@@ -139,7 +139,7 @@ def test_pcg_fp32_galerkin_vs_float64_oracle(vfp32):
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         st, info = B.amg_pcg_solve(h, dev(b), x, rtol=1e-8, itmax=500)
         assert st == B.AMG_OK and info["rel_res_true"] <= 2e-8
-        assert it32 - 1 <= info["iters"] <= it32 + (3 if vfp32 else 1)
+        assert abs(info["iters"] - it32) <= 1
         assert info["iters"] <= it64 + 2 + (2 if vfp32 else 0)
         assert np.linalg.norm(host(x) - xs) / np.linalg.norm(xs) < 1e-5
         compared = 0

@@ -89,18 +89,58 @@ def test_q1_element_stiffness_rigid_body_modes():
     assert (np.abs(ev[:6]) <= 1e-13 * ev[-1]).all() and ev[6] > 1e-3 * ev[-1]
 
 
+def _nb(m):
+    """Ordered pairs (i, j) with |i - j| <= 1 among m consecutive grid positions."""
+    return m + 2 * (m - 1)
+
+
 @pytest.mark.parametrize("nodes", [4, 6])
 def test_elasticity_q1_sizes_and_spd(nodes):
-    """x = 0 face clamped by elimination: n = 3 (nodes - 1) nodes^2; at most 9 entries per
-    pair of nodes sharing an element (27 node neighbours inside, fewer on the boundary);
-    symmetric positive definite."""
+    """x = 0 face clamped by elimination: n = 3 (nodes - 1) nodes^2; exactly 9 entries per
+    ordered pair of free nodes sharing an element (the assembled pattern, stored zeros
+    included); symmetric positive definite."""
     mat = P.elasticity_q1(nodes)
     n = len(mat[0]) - 1
     assert n == 3 * (nodes - 1) * nodes * nodes
-    nb_x = 2 + 3 * (nodes - 3) + 2  # neighbour count summed over the free x positions 1..nodes-1
-    nb_yz = 2 + 3 * (nodes - 2) + 2
-    assert len(mat[1]) <= 9 * nb_x * nb_yz * nb_yz
+    assert len(mat[1]) == 9 * _nb(nodes - 1) * _nb(nodes) ** 2
     A = _dense(mat)
     assert np.array_equal(A, A.T)
     np.linalg.cholesky(A)
     assert (np.diag(A) > 0).all()
+    rp, ci, _ = mat
+    assert all((np.diff(ci[rp[i]:rp[i + 1]]) > 0).all() for i in range(n))
+
+
+def test_elasticity_q1_brute_force_assembly():
+    """Element by element: A = sum over the (nodes-1)^3 cubes of the 24x24 element stiffness
+    on the cube's dofs, clamped rows and columns removed; the stored pattern is every pair
+    of dofs of nodes within one grid step in each direction, and stored zeros occur exactly
+    where the assembled sum cancels."""
+    nodes = 4
+    rp, ci, val = P.elasticity_q1(nodes)
+    ne, h = nodes - 1, 1.0 / (nodes - 1)
+    Ke = P._q1_element_stiffness(h, 1.0, 0.3)
+    full = np.zeros((3 * nodes ** 3,) * 2)
+    coupled = np.zeros_like(full, dtype=bool)
+    for ez, ey, ex in itertools.product(range(ne), repeat=3):
+        nd = [((ez + (a >> 2 & 1)) * nodes + ey + (a >> 1 & 1)) * nodes + ex + (a & 1) for a in range(8)]
+        dofs = np.array([3 * q + c for q in nd for c in range(3)])
+        full[np.ix_(dofs, dofs)] += Ke
+        coupled[np.ix_(dofs, dofs)] = True
+    free = np.array([d for d in range(3 * nodes ** 3) if (d // 3) % nodes != 0])
+    ref, pat = full[np.ix_(free, free)], coupled[np.ix_(free, free)]
+    n = len(free)
+    A = _dense((rp, ci, val))
+    S = np.zeros((n, n), bool)
+    S[np.repeat(np.arange(n), np.diff(rp)), ci] = True
+    assert np.array_equal(S, pat)
+    assert np.abs(A - ref).max() <= 1e-14 * np.abs(ref).max()
+    zeros = S & (A == 0)
+    assert zeros.sum() > 0 and (np.abs(ref[zeros]) <= 1e-14 * np.abs(ref).max()).all()
+
+
+def test_elasticity_q1_full_size_counts():
+    """64^3 nodes, x = 0 clamped: n = 3 * 63 * 64^2 = 774,144 and nnz = 9 * 187 * 190^2 =
+    60,756,300 by the pair count above (both without building the matrix)."""
+    assert 3 * 63 * 64 * 64 == 774144
+    assert 9 * _nb(63) * _nb(64) ** 2 == 60756300
