@@ -2,9 +2,11 @@
 pre/post sweep counts, and the float32 V-cycle inside the float64 FCG.
 
 Tolerances: float64 V-cycle 1e-12 relative (summation order differs from the oracle's);
-float32 V-cycle 2e-5 relative to the float64 oracle (unit roundoff 6e-8 times the
-work per row and the levels); FCG with the float32 V-cycle must still reach 1e-8 within
-one iteration of the oracle's float64 run.
+float32 V-cycle FP32_TOL = 1e-6 relative to the float64 oracle, about 17 binary32 unit
+roundoffs (u = 2^-24): the largest error measured over every input here, every tail,
+A P and W-cycle setting, was 1.6e-7 (2.6u, Q1 elasticity 8^3 nodes); FCG with the
+float32 V-cycle must still reach 1e-8 within one iteration of the oracle's float64 run
+(measured: the same count on every input).
 """
 import numpy as np
 import pytest
@@ -16,6 +18,7 @@ from tests.gpu_util import csr_dev, dev, host
 
 pytestmark = pytest.mark.gpu
 B = None
+FP32_TOL = 1e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -98,7 +101,7 @@ def test_long_row_split_coarsest(fp32):
     mat = P.random_spd_hubs(5000, 4.0, n_hubs=12, hub_degree=300, seed=7)
     assert _long_rows(mat) >= 12
     got, ref = _vcycle_pair(mat, 2, 10_000, dict(tail_rows=-1, vcycle_fp32=fp32))
-    tol = 2e-5 if fp32 else 1e-12
+    tol = FP32_TOL if fp32 else 1e-12
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
 
 
@@ -107,7 +110,7 @@ def test_long_row_split_hierarchy(fp32):
     """Hub rows on every level of a multi-level hierarchy (post-smoothing sweeps split too)."""
     mat = P.random_spd_hubs(20000, 4.0, n_hubs=40, hub_degree=400, seed=8)
     got, ref = _vcycle_pair(mat, 2, 60, dict(tail_rows=-1, vcycle_fp32=fp32))
-    tol = 2e-5 if fp32 else 1e-12
+    tol = FP32_TOL if fp32 else 1e-12
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
 
 
@@ -144,7 +147,7 @@ def test_vcycle_coupled_post(case, coupled, fp32):
     finally:
         h.free()
     ref = H.vcycle(r)
-    assert np.abs(got - ref).max() <= (2e-5 if fp32 else 1e-12) * np.abs(ref).max()
+    assert np.abs(got - ref).max() <= (FP32_TOL if fp32 else 1e-12) * np.abs(ref).max()
     # level 0 through A P: a pre-sweep `scale` and no separate post-sweep `jacobi`
     used = "scale@0" in names and "jacobi@0" not in names
     if name.startswith("poisson3d"):  # 7-entry rows: auto mode leaves them to the separate passes
@@ -184,7 +187,7 @@ def test_pcg_and_wcycle_coupled_post(coupled):
 def test_vcycle_fp32(case, tail_rows):
     name, gen, sweeps, cmax = case
     got, ref = _vcycle_pair(gen(), sweeps, cmax, dict(vcycle_fp32=1, tail_rows=tail_rows))
-    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert np.abs(got - ref).max() <= FP32_TOL * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -241,7 +244,7 @@ def test_wcycle_matches_oracle(gen, sweeps, cmax, fp32):
         w = torch.empty(n, dtype=torch.float64, device="cuda")
         got = host(B.amg_vcycle(h, dev(r), w))
         ref = H.vcycle(r)
-        assert np.abs(got - ref).max() <= (2e-5 if fp32 else 1e-12) * np.abs(ref).max()
+        assert np.abs(got - ref).max() <= (FP32_TOL if fp32 else 1e-12) * np.abs(ref).max()
         xs, b = P.manufactured_rhs(*mat, seed=4)
         xr, st_r, it_r, _, _ = H.pcg(b, rtol=1e-8, itmax=300)
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
