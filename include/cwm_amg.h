@@ -193,12 +193,13 @@ amg_status cwm_suitor_match(int n, int64_t nnz, const int32_t *d_row_ptr, const 
  * vertex come from a fixed array inside the library (16 MiB, held by every GPU that loads
  * the library until the process exits), so no call allocates or frees device memory.
  *   - n is limited to 1,048,576 vertices; larger n returns AMG_ERR_UNSUPPORTED.
- *   - The first call on a device looks up the array's device address for that device;
- *     make that first call before any stream capture.
+ *   - Every call looks up the array's address on the current device (no allocation), so
+ *     the call stays valid after the host application resets the device.
  *   - Every call uses the same array, so calls whose GPU work overlaps (different streams,
  *     or different threads on one device) race and corrupt each other's result; order
  *     them on one stream.  The scratch contents left by a call are cleared by the next.
- * Synchronises. */
+ * Synchronises (it reads the device error word back): do not call it while `stream` is
+ * being captured into a CUDA graph. */
 amg_status cwm_suitor_match_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr,
                                    const int32_t *d_col, const double *d_w, int32_t *d_mate,
                                    void *stream);

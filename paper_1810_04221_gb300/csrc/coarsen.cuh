@@ -22,6 +22,9 @@ amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, 
 amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, const double *val,
                         const double *diag, const double *v, double *w, double *dv_scratch, cudaStream_t s,
                         bool clear = true);
+// Suitor matching (Sec. 3.1) into mate[n].  scratch: suitor_scratch_bytes(n) bytes (16 per
+// vertex, the packed suitor keys), which suitor_match clears itself before the proposals
+// start, so it may hold anything on entry; d_err: the device error word (not cleared here).
 size_t suitor_scratch_bytes(int n);
 amg_status suitor_match(int n, long long nnz, const int *rp, const int *ci, const double *w,
                         void *scratch, int *mate, long long cap, int *d_err, cudaStream_t s);

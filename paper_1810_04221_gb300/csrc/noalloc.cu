@@ -5,8 +5,6 @@
 // variant takes it from the file-scope array below instead, so a call makes no device
 // allocation and frees nothing.  The array is sized for kNoAllocMaxVertices vertices and
 // is held by every GPU that loads this library until the process exits.
-#include <mutex>
-
 #include "coarsen.cuh"
 
 namespace cwm {
@@ -20,26 +18,15 @@ constexpr size_t kScratchBytes = kKeyBytes + 256;                  // + the erro
 // address is obtained with cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_suitor_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {nullptr};
-
-// Resolves the scratch array's device address once per device, with that device current.
+// The scratch array's device address on the current device, looked up on every call (a
+// host-side table lookup that allocates nothing): an address kept from an earlier call
+// would be stale after the host application resets the device (cudaDeviceReset), and a
+// kernel given it would fault.
 amg_status scratch_address(void **out) {
-  int dev = 0;
-  CWM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("cwm_suitor_match_noalloc: device ordinal %d beyond %d", dev, kMaxDevices);
-    return AMG_ERR_UNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_suitor_scratch);
-    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(g_suitor_scratch)", __FILE__, __LINE__);
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_suitor_scratch);
+  if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(g_suitor_scratch)", __FILE__, __LINE__);
+  *out = p;
   return AMG_OK;
 }
 
@@ -65,8 +52,8 @@ extern "C" amg_status cwm_suitor_match_noalloc(int n, int64_t nnz, const int32_t
   void *base = nullptr;
   CWM_TRY(scratch_address(&base));
   int *d_err = reinterpret_cast<int *>(static_cast<unsigned char *>(base) + kKeyBytes);
-  // the array keeps the previous call's contents: the error word is cleared here and the
-  // keys are cleared by suitor_match before the proposals start
+  // the array keeps the previous call's contents: the error word is cleared here, and
+  // suitor_match clears the first n keys itself before the proposals start
   CWM_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   CWM_TRY(suitor_match(n, nnz, d_row_ptr, d_col, d_w, base, d_mate, nnz + n + 1024, d_err, s));
   int h_err = 0;
