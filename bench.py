@@ -218,6 +218,8 @@ def run_cuda(args, rank, world, dist):
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
+    extra = dict(extra, block3=args.block3)
+
     def params(trace=0, filt=""):
         return B.amg_default_params(sweeps_per_level=sweeps, coarse_max=cmax, vcycle_fp32=int(fp32), trace=trace,
                                     trace_filter=filt, check_input=0, **extra)
@@ -520,6 +522,8 @@ def main():
     ap.add_argument("--variant", type=int, default=1,
                     help="also time the precision variants (other V-cycle precision; binary32 Galerkin)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block3", type=int, default=0, choices=[0, -1],
+                    help="3x3-block layout of the finest operator: 0 auto (when its pattern qualifies), -1 never")
     ap.add_argument("--oracle-check", type=int, default=1,
                     help="solve the full-size system with the oracle too (spawned worker) and report each "
                          "result's distance to its solution")

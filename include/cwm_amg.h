@@ -93,6 +93,13 @@ typedef struct {
                            gains); 1 = every level below the coarsest;
                            -1 = off.  Levels with rows longer than 1024 entries never
                            take it. */
+  int block3;           /* 0 = auto (default): when every block row of the input operator
+                           (rows 3b, 3b+1, 3b+2) stores the same columns in whole aligned
+                           triples (3c, 3c+1, 3c+2) -- a nodal 3D vector problem with
+                           interleaved unknowns and its assembled pattern -- the finest
+                           level's residual in the V-cycle and the FCG's SpMV with its dot
+                           products stream a copy of it in 3x3 blocks (one column index
+                           per block; the same products summed in block order); -1 = never */
 } amg_params;
 
 /* Statistics filled by amg_pcg_solve and amg_stats. */

@@ -48,6 +48,7 @@ class AmgParams(C.Structure):
         ("gamma", C.c_int),
         ("galerkin_fp32_from", C.c_int),
         ("coupled_post", C.c_int),
+        ("block3", C.c_int),
     ]
 
 

@@ -50,6 +50,11 @@ struct Level {
   DBuf<float> ap_val32;
   long long ap_nnz = 0;
   int ap_max_row = 0;
+  // the finest operator in 3x3 blocks (block3.cu), when its pattern is 3x3-blocked
+  DBuf<int> b3_sptr, b3_blen, b3_bci;
+  DBuf<double> b3_val;
+  DBuf<float> b3_val32;
+  long long b3_slots = 0;
 
   template <class V>
   void split(CsrView<V> &a, bool fp64) const {
@@ -73,6 +78,20 @@ struct Level {
     a.n = n; a.nnz = nnz; a.rp = rp.get(); a.ci = ci.get(); a.val = val32.get();
     row_kernel_shape(n, nnz, max_row, false, &a.rb, &a.tile);
     split(a, false);
+    return a;
+  }
+  template <class V>
+  Sell3View<V> block3_view(const V *values) const {
+    Sell3View<V> a;
+    if (!values) return a;  // nbr = 0: no block layout
+    a.n = n;
+    a.nbr = n / 3;
+    a.nblocks = nnz / 9;
+    a.slots = b3_slots;
+    a.sptr = b3_sptr.get();
+    a.blen = b3_blen.get();
+    a.bci = b3_bci.get();
+    a.val = values;
     return a;
   }
   template <class V>
@@ -436,6 +455,47 @@ amg_status build_ap(amg_hierarchy *h) {
   return AMG_OK;
 }
 
+// The finest operator in 3x3 blocks (block3.cu), when its pattern qualifies and block3 >= 0:
+// one synchronisation reads the detection flag and the per-slice lengths; the slice offsets
+// are scanned on the host.
+amg_status build_block3(amg_hierarchy *h) {
+  Level &L = h->lev[0];
+  if (h->prm.block3 < 0 || L.n < 3 || L.n % 3 != 0 || L.nnz % 9 != 0) return AMG_OK;
+  cudaStream_t s = h->stream;
+  LevelTag tag(0);
+  const int nbr = L.n / 3, nsl = (nbr + 31) / 32;
+  DBuf<int> smax;
+  CWM_TRY(smax.alloc(nsl, s));
+  CWM_CUDA(cudaMemsetAsync(smax.get(), 0, sizeof(int) * (size_t)nsl, s));
+  int *flag = h->err.get() + 1;  // scratch word next to the error bits
+  CWM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  CWM_TRY(block3_detect(L.n, L.rp.get(), L.ci.get(), flag, smax.get(), s));
+  std::vector<int> hs((size_t)nsl + 1, 0);
+  CWM_CUDA(cudaMemcpyAsync(h->box.ints + 6, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CWM_CUDA(cudaMemcpyAsync(hs.data(), smax.get(), sizeof(int) * (size_t)nsl, cudaMemcpyDeviceToHost, s));
+  CWM_TRY(read_err(h, "amg_setup (3x3 blocks)"));  // synchronises
+  if (h->box.ints[6] != 0) return AMG_OK;          // not 3x3-blocked: the CSR kernels serve
+  long long slots = 0;
+  for (int q = 0; q < nsl; ++q) {
+    const long long len = hs[q];
+    hs[q] = (int)slots;
+    slots += 32 * len;
+    if (slots >= (long long)INT32_MAX) return AMG_OK;  // slot offsets are int32
+  }
+  hs[nsl] = (int)slots;
+  CWM_TRY(L.b3_sptr.alloc((size_t)nsl + 1, s));
+  CWM_CUDA(cudaMemcpyAsync(L.b3_sptr.get(), hs.data(), sizeof(int) * ((size_t)nsl + 1), cudaMemcpyHostToDevice, s));
+  CWM_TRY(L.b3_blen.alloc(nbr, s));
+  CWM_TRY(L.b3_bci.alloc((size_t)slots, s));
+  CWM_TRY(L.b3_val.alloc(9 * (size_t)slots, s));
+  if (h->prm.vcycle_fp32) CWM_TRY(L.b3_val32.alloc(9 * (size_t)slots, s));
+  L.b3_slots = slots;
+  CWM_TRY(block3_fill(L.n, L.rp.get(), L.ci.get(), L.val.get(), L.b3_sptr.get(), L.b3_blen.get(), L.b3_bci.get(),
+                      L.b3_val.get(), L.b3_val32.get(), slots, s));
+  CWM_CUDA(cudaStreamSynchronize(s));  // hs is released on return
+  return AMG_OK;
+}
+
 amg_status finish_level(amg_hierarchy *h, Level &L) {
   cudaStream_t s = h->stream;
   {  // the long rows of a sub-warp-tile level (see long_row_min)
@@ -500,6 +560,7 @@ struct LevelVec<double> {
   static const double *dense(const Level &L) { return L.xdense.get(); }
   static bool has_ap(const Level &L) { return L.ap_nnz > 0 && L.ap_val.get(); }
   static CsrView<double> AP(const Level &L) { return L.ap_view<double>(L.ap_val.get()); }
+  static Sell3View<double> B3(const Level &L) { return L.block3_view<double>(L.b3_val.get()); }
 };
 template <>
 struct LevelVec<float> {
@@ -513,6 +574,7 @@ struct LevelVec<float> {
   static const float *dense(const Level &L) { return L.xdense32.get(); }
   static bool has_ap(const Level &L) { return L.ap_nnz > 0 && L.ap_val32.get(); }
   static CsrView<float> AP(const Level &L) { return L.ap_view<float>(L.ap_val32.get()); }
+  static Sell3View<float> B3(const Level &L) { return L.block3_view<float>(L.b3_val32.get()); }
 };
 
 template <>
@@ -627,7 +689,19 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   // level with A P (built for the levels that skip the fused kernels, or for every level with
   // coupled_post = 1) takes the coarse correction and the post-sweep through it instead.
   const bool ap = h->prm.post_sweeps == 1 && LV::has_ap(L);
-  if (!ap && zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 && A.n <= fuse_max_rows<V>() && A.rb) {
+  // the finest operator in 3x3 blocks: the residual streams the block layout
+  const Sell3View<V> B3 = k == 0 ? LV::B3(L) : Sell3View<V>{};
+  if (B3.nbr > 0 && ap && zero_init && h->prm.pre_sweeps == 1) {
+    // the first sweep from zero, xs = D^{-1} b, formed on the fly inside the residual
+    // r = b - A xs and inside the coarse correction + post-sweep through A P
+    Level &C = h->lev[k + 1];
+    CWM_TRY(block3_resid_restrict<V>(B3, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, nullptr, dinv, t1,
+                                     LV::b(C), s));
+    for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C), LV::x(C), g == 0));
+    return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, t1, L.agg.get(), LV::p(L), LV::x(C), b, true, x, s);
+  }
+  if (!ap && B3.nbr == 0 && zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 &&
+      A.n <= fuse_max_rows<V>() && A.rb) {
     CWM_TRY(resid_scaled_restrict<V>(A, C0.n, L.mptr.get(), L.mlist.get(), LV::p(L), dinv, b, t1, LV::b(C0), s));
     for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C0), LV::x(C0), g == 0));
     return prolong_jacobi<V>(A, dinv, b, L.agg.get(), LV::p(L), LV::x(C0), x, s);
@@ -642,10 +716,14 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   }
   Level &C = h->lev[k + 1];
   V *rtmp = (xs == t1) ? t2 : t1;  // free until the prolongation writes it
-  CWM_TRY(resid_restrict_rb<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, rtmp, LV::b(C), s));
+  if (B3.nbr > 0 && xs)
+    CWM_TRY(block3_resid_restrict<V>(B3, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, nullptr, rtmp, LV::b(C),
+                                     s));
+  else
+    CWM_TRY(resid_restrict_rb<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, rtmp, LV::b(C), s));
   for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C), LV::x(C), g == 0));
   if (ap)  // rtmp still holds b - A xs
-    return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, rtmp, L.agg.get(), LV::p(L), LV::x(C), xs, x, s);
+    return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, rtmp, L.agg.get(), LV::p(L), LV::x(C), xs, false, x, s);
   V *y = (xs == t1) ? t2 : t1;
   CWM_TRY(prolong<V>(A.n, L.agg.get(), LV::p(L), LV::x(C), xs, y, s));
   const int post = h->prm.post_sweeps;
@@ -702,6 +780,7 @@ void amg_default_params(amg_params *p) {
   p->gamma = 1;
   p->galerkin_fp32_from = 0;
   p->coupled_post = 0;
+  p->block3 = 0;
 }
 
 const char *amg_status_string(amg_status s) {
@@ -791,6 +870,7 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
     if (P.stall_ratio > 0.0 && (double)Fl.n < P.stall_ratio * (double)Cl.n) break;
   }
   for (Level &L : h->lev) CWM_TRY(finish_level(h, L));
+  CWM_TRY(build_block3(h));
   h->lev.back().nsweeps = 0;
   {
     Level &Lc = h->lev.back();
@@ -994,8 +1074,13 @@ amg_status fcg_iteration(amg_hierarchy *h, double *d_x, int first) {
   const CsrView<double> A = L0.view64();
   double *scal = h->scal.get();
   CWM_TRY(apply_vcycle(h, h->r.get(), h->w.get()));
-  CWM_TRY(spmv_dots_scalars(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
-                            scal, h->tick.get(), first, s));
+  const Sell3View<double> B3 = LevelVec<double>::B3(L0);
+  if (B3.nbr > 0)
+    CWM_TRY(block3_spmv_dots(B3, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
+                             fcg_dots_blocks_max(L0.n, L0.nnz), scal, h->tick.get(), first, s));
+  else
+    CWM_TRY(spmv_dots_scalars(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
+                              scal, h->tick.get(), first, s));
   CWM_TRY(fcg_update(L0.n, h->w.get(), h->vv.get(), h->d.get(), h->q.get(), d_x, h->r.get(), scal, h->part2.get(),
                      h->tick.get() + 1, first, s));
   CWM_CUDA(cudaMemcpyAsync(h->box.dbls, scal, sizeof(double) * kFcgSlots, cudaMemcpyDeviceToHost, s));

@@ -4,6 +4,7 @@
 // Sec. 3.2 (three dot products in one pass with the SpMV, paired vector updates).
 #include <algorithm>
 
+#include "fcg.cuh"
 #include "solve.cuh"
 
 namespace cwm {
@@ -85,6 +86,7 @@ __device__ __forceinline__ double block_sum(double v) {
 // retires about 500 G instructions/s (a DMUL + DADD pair per nonzero would make the FP64
 // SpMV compute-bound).
 constexpr int kRB = 256;
+static_assert(kRB == kRedBlock, "the row-block kernels reduce with block_sums (fcg.cuh)");
 constexpr int kRBE = 8;
 constexpr int kRBC = kRB * kRBE;
 
@@ -288,32 +290,6 @@ amg_status max_row_length(int n, const int *rp, int *d_out, cudaStream_t s) {
   return AMG_OK;
 }
 
-// Block sums of up to three values per thread with few FP64 instructions (blockDim ==
-// kRB): the values go to shared memory, then warp w folds value w (kRB/32 sequential adds
-// per lane and five shuffle steps).  GB300 retires FP64 adds as whole-warp instructions at
-// a low rate, so this beats a shuffle tree in every warp.  Results valid in every thread.
-template <int NV>
-__device__ __forceinline__ void block_sums(const double (&in)[NV], double (&out)[NV]) {
-  __shared__ double s_in[NV][kRB];
-  __shared__ double s_out[NV];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) s_in[v][threadIdx.x] = in[v];
-  __syncthreads();
-  if (w < NV) {
-    double a = 0.0;
-#pragma unroll
-    for (int k = 0; k < kRB / 32; ++k) a += s_in[w][lane * (kRB / 32) + k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) s_out[w] = a;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < NV; ++v) out[v] = s_out[v];
-  __syncthreads();
-}
-
 // ------------------------------------------------------------ elementwise ----
 template <class V>
 __global__ void k_scale(int n, const V *__restrict__ dinv, const V *__restrict__ b, V *__restrict__ y) {
@@ -485,8 +461,15 @@ amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, c
     CWM_CUDA(launch_pdl(k_resid_scaled_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, r_scratch));
     CWM_LAUNCH();
   }
-  CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
-  CWM_CUDA(launch_pdl(k_restrict<V>, grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s, nc, mptr, mlist, p, r_scratch, bc));
+  return restrict_members<V>(A.n, nc, mptr, mlist, p, r_scratch, bc, s);
+}
+
+template <class V>
+amg_status restrict_members(int n, int nc, const int *mptr, const int *mlist, const V *p, const V *r, V *bc,
+                            cudaStream_t s) {
+  if (nc == 0) return AMG_OK;
+  CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * n + (4.0 + sizeof(V)) * nc, s);
+  CWM_CUDA(launch_pdl(k_restrict<V>, grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s, nc, mptr, mlist, p, r, bc));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -698,8 +681,9 @@ amg_status ap_group(int n, long long nnz, const int *rp, const int *ci, const do
 
 // The coarse correction and the first post-sweep through A P:  with y = xs + P xc and
 // r = b - A xs (the residual the restriction took), b - A y = r - (A P) xc, so
-// x = y + D^{-1} (r - (A P) xc).  xs may be NULL (0).
-template <class V>
+// x = y + D^{-1} (r - (A P) xc).  xs may be NULL (0); XS_SCALED: xs holds b and the
+// pre-sweep result D^{-1} b is formed on the fly (rounded as the scale kernel rounds it).
+template <class V, bool XS_SCALED>
 __global__ void __launch_bounds__(kRB) k_prolong_jacobi_ap_rb(int n, const int *__restrict__ rp,
                                                               const int *__restrict__ ci, const V *__restrict__ val,
                                                               const V *__restrict__ dinv, const V *__restrict__ r,
@@ -718,13 +702,13 @@ __global__ void __launch_bounds__(kRB) k_prolong_jacobi_ap_rb(int n, const int *
   if (in) {
     ri = r[i];
     di = dinv[i];
-    yi = fma(p[i], __ldg(xc + agg[i]), xs ? xs[i] : V(0));
+    yi = fma(p[i], __ldg(xc + agg[i]), xs ? (XS_SCALED ? di * xs[i] : xs[i]) : V(0));
   }
   const V res = rb_row_dot<V, false, true>(ci, val, xc, nrows, sm, ri);
   if (in) x[i] = fma(di, res, yi);
 }
 
-template <class V, int T>
+template <class V, int T, bool XS_SCALED>
 __global__ void __launch_bounds__(kBlock)
     k_prolong_jacobi_ap(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ val,
                         const V *__restrict__ dinv, const V *__restrict__ r, const int *__restrict__ agg,
@@ -738,26 +722,34 @@ __global__ void __launch_bounds__(kBlock)
     if (active && lane == 0) {
       ri = r[row];
       di = dinv[row];
-      yi = fma(p[row], __ldg(xc + agg[row]), xs ? xs[row] : V(0));
+      yi = fma(p[row], __ldg(xc + agg[row]), xs ? (XS_SCALED ? di * xs[row] : xs[row]) : V(0));
     }
     const V res = tile_row_dot<V, T, true>(rp, ci, val, xc, row, active, lane, ri);
     if (active && lane == 0) x[row] = fma(di, res, yi);
   }
 }
 
+template <class V, bool XS_SCALED>
+static amg_status launch_prolong_jacobi_ap(const CsrView<V> &AP, const V *dinv, const V *r, const int *agg,
+                                           const V *p, const V *xc, const V *xs, V *x, cudaStream_t s) {
+  if (AP.rb) {
+    CWM_CUDA(launch_pdl(k_prolong_jacobi_ap_rb<V, XS_SCALED>, rb_grid(AP.n), kRB, 0, s, AP.n, AP.rp, AP.ci, AP.val,
+                        dinv, r, agg, p, xc, xs, x));
+  } else {
+    CWM_DISPATCH_T(AP.tile, CWM_CUDA(launch_pdl(k_prolong_jacobi_ap<V, kT, XS_SCALED>, rows_grid(AP.n, kT), kBlock, 0,
+                                                s, AP.n, AP.rp, AP.ci, AP.val, dinv, r, agg, p, xc, xs, x)));
+  }
+  return AMG_OK;
+}
+
 template <class V>
 amg_status prolong_jacobi_ap(const CsrView<V> &AP, int nc, const V *dinv, const V *r, const int *agg, const V *p,
-                             const V *xc, const V *xs, V *x, cudaStream_t s) {
+                             const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s) {
   if (AP.n == 0) return AMG_OK;
   CWM_TRACE("prolong_jacobi", 4.0 * (AP.n + 1) + (4.0 + sizeof(V)) * AP.nnz +
                                   ((xs ? 5.0 : 4.0) * sizeof(V) + 4.0) * AP.n + sizeof(V) * (double)nc, s);
-  if (AP.rb) {
-    CWM_CUDA(launch_pdl(k_prolong_jacobi_ap_rb<V>, rb_grid(AP.n), kRB, 0, s, AP.n, AP.rp, AP.ci, AP.val, dinv, r, agg, p,
-                        xc, xs, x));
-  } else {
-    CWM_DISPATCH_T(AP.tile, CWM_CUDA(launch_pdl(k_prolong_jacobi_ap<V, kT>, rows_grid(AP.n, kT), kBlock, 0, s, AP.n, AP.rp,
-                                                AP.ci, AP.val, dinv, r, agg, p, xc, xs, x)));
-  }
+  if (xs_scaled) CWM_TRY((launch_prolong_jacobi_ap<V, true>(AP, dinv, r, agg, p, xc, xs, x, s)));
+  else CWM_TRY((launch_prolong_jacobi_ap<V, false>(AP, dinv, r, agg, p, xc, xs, x, s)));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -853,11 +845,9 @@ amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const
     CWM_TRY(launch_residual<V>(A, b, x, r_scratch, s));
     CWM_LAUNCH();
   }
-  CWM_TRACE("restrict", (4.0 + 2.0 * sizeof(V)) * A.n + (4.0 + sizeof(V)) * nc, s);
-  CWM_CUDA(launch_pdl(k_restrict<V>, grid_for(nc, kBlock, num_sms() * 8), kBlock, 0, s, nc, mptr, mlist, p, r_scratch, bc));
-  CWM_LAUNCH();
-  return AMG_OK;
+  return restrict_members<V>(A.n, nc, mptr, mlist, p, r_scratch, bc, s);
 }
+
 
 // ------------------------------------------------------------ coarsest solve ----
 // One block; x ping-pongs between two shared-memory copies; thread per row.
@@ -1101,73 +1091,6 @@ int fcg_partial_blocks(int n) {
 constexpr int kUpdChunk = 8 * kRB;  // entries per fcg_update block
 int fcg_update_blocks(int n) { return (int)(((n > 0 ? n : 1) + kUpdChunk - 1LL) / kUpdChunk); }
 
-// The block that finishes last (atomic ticket after a fence) reduces every block's partial
-// sums in block order -- a fixed order, so the result does not depend on scheduling -- and
-// resets the ticket for the next launch.
-__device__ __forceinline__ bool last_block(unsigned *tick) {
-  __shared__ bool s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(tick, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) __threadfence();
-  return s_last;
-}
-
-// Sum of part[stride * i + c] over i = threadIdx.x, threadIdx.x + blockDim.x, ... < nb, in
-// that order; the L2 loads of four iterations are issued before their adds (this runs on
-// the critical path, in the last block, after every other block has finished).
-template <int STRIDE, int C>
-__device__ __forceinline__ double strided_sum(int nb, const double *part) {
-  double a = 0.0;
-  int i = threadIdx.x;
-  const int bd = blockDim.x;
-  for (; i + 3 * bd < nb; i += 4 * bd) {
-    const double t0 = __ldcg(part + STRIDE * i + C), t1 = __ldcg(part + STRIDE * (i + bd) + C);
-    const double t2 = __ldcg(part + STRIDE * (i + 2 * bd) + C), t3 = __ldcg(part + STRIDE * (i + 3 * bd) + C);
-    a += t0;
-    a += t1;
-    a += t2;
-    a += t3;
-  }
-  for (; i < nb; i += bd) a += __ldcg(part + STRIDE * i + C);
-  return a;
-}
-
-__device__ __forceinline__ void fcg_scalars_from(int nb, const double *part, double *scal, int first) {
-  double a = strided_sum<3, 0>(nb, part), b = strided_sum<3, 1>(nb, part), g = strided_sum<3, 2>(nb, part);
-  {
-    const double in3[3] = {a, b, g};
-    double o3[3];
-    block_sums<3>(in3, o3);
-    a = o3[0];
-    b = o3[1];
-    g = o3[2];
-  }
-  if (threadIdx.x == 0) {
-    double rho, coef;
-    if (first) {
-      rho = b;
-      coef = 0.0;
-      g = 0.0;
-    } else {
-      const double rp = scal[kRhoPrev];
-      rho = b - g * g / rp;
-      coef = g / rp;
-    }
-    scal[kAlpha] = a;
-    scal[kBeta] = b;
-    scal[kGamma] = g;
-    scal[kRho] = rho;
-    scal[kCoef] = coef;
-    scal[kStep] = a / rho;
-    scal[kRhoPrev] = rho;
-    if (!(rho > 0.0) || !isfinite(rho) || !isfinite(a)) scal[kFlags] = 1.0;
-  }
-}
-
 __global__ void __launch_bounds__(kRB)
     k_spmv_dots_rb(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ val,
                    const double *__restrict__ w, const double *__restrict__ r, const double *__restrict__ q,
@@ -1192,18 +1115,7 @@ __global__ void __launch_bounds__(kRB)
       if (q) sg = fma(wi, qi, sg);
     }
   }
-  const double in3[3] = {sa, sb, sg};
-  double t3[3];
-  block_sums<3>(in3, t3);
-  if (threadIdx.x == 0) {
-    part[3 * blockIdx.x + 0] = t3[0];
-    part[3 * blockIdx.x + 1] = t3[1];
-    part[3 * blockIdx.x + 2] = t3[2];
-  }
-  if (last_block(tick)) {
-    fcg_scalars_from(gridDim.x, part, scal, first);
-    if (threadIdx.x == 0) *tick = 0u;
-  }
+  fcg_dots_finish(sa, sb, sg, part, scal, tick, first);
 }
 
 // Same with a sub-warp tile per row (levels on sub-warp tiles, see row_blocks_for).
@@ -1226,18 +1138,7 @@ __global__ void __launch_bounds__(kBlock)
       if (q) sg = fma(wi, q[row], sg);
     }
   }
-  const double in3[3] = {sa, sb, sg};
-  double t3[3];
-  block_sums<3>(in3, t3);
-  if (threadIdx.x == 0) {
-    part[3 * blockIdx.x + 0] = t3[0];
-    part[3 * blockIdx.x + 1] = t3[1];
-    part[3 * blockIdx.x + 2] = t3[2];
-  }
-  if (last_block(tick)) {
-    fcg_scalars_from(gridDim.x, part, scal, first);
-    if (threadIdx.x == 0) *tick = 0u;
-  }
+  fcg_dots_finish(sa, sb, sg, part, scal, tick, first);
 }
 
 #ifndef CWM_DOTS_RB_MAX_MEAN
@@ -1422,8 +1323,10 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
   template amg_status prolong_jacobi<V>(const CsrView<V> &, const V *, const V *, const int *, const V *,    \
                                         const V *, V *, cudaStream_t);                                       \
   template amg_status prolong_jacobi_ap<V>(const CsrView<V> &, int, const V *, const V *, const int *, const V *, \
-                                           const V *, const V *, V *, cudaStream_t);                          \
-  template amg_status add_to<V>(int, const V *, V *, cudaStream_t);
+                                           const V *, const V *, bool, V *, cudaStream_t);                    \
+  template amg_status add_to<V>(int, const V *, V *, cudaStream_t);                                          \
+  template amg_status restrict_members<V>(int, int, const int *, const int *, const V *, const V *, V *,      \
+                                          cudaStream_t);
 CWM_INST(double)
 CWM_INST(float)
 

@@ -82,10 +82,11 @@ amg_status ap_group(int n, long long nnz, const int *rp, const int *ci, const do
                     const double *p, int max_row, int *ci_pad, double *val_pad, int *cnt, int *maxcnt,
                     cudaStream_t s);
 // x = y + D^{-1} (r - (A P) xc) with y = xs + P xc and r = b - A xs: the coarse correction
-// and one post-sweep (xs may be NULL: 0); AP: the stored product A P, nc: columns of P
+// and one post-sweep (xs may be NULL: 0; xs_scaled: xs holds b and the pre-sweep result is
+// D^{-1} b); AP: the stored product A P, nc: columns of P
 template <class V>
 amg_status prolong_jacobi_ap(const CsrView<V> &AP, int nc, const V *dinv, const V *r, const int *agg, const V *p,
-                             const V *xc, const V *xs, V *x, cudaStream_t s);
+                             const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s);
 // r = b - A x (any value type)
 template <class V>
 amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s);
@@ -130,6 +131,46 @@ amg_status vcycle_tail(const TailArgs<V> &a, const TailArgs<V> *d_a, const V *b0
                        cudaStream_t s);
 // r = b - A x
 amg_status residual(const CsrView<double> &A, const double *b, const double *x, double *r, cudaStream_t s);
+// bc[I] = sum over the members m of aggregate I (ascending) of p_m r_m (the restriction P^T r)
+template <class V>
+amg_status restrict_members(int n, int nc, const int *mptr, const int *mlist, const V *p, const V *r, V *bc,
+                            cudaStream_t s);
+
+// ---------------------------------------------------------------- 3x3 blocks ----
+// An operator whose block rows (rows 3b, 3b+1, 3b+2) all store the same columns in whole
+// aligned triples, held as 3x3 blocks in a sliced-ELL layout over 32 block rows (block3.cu):
+// block row b's t-th block at slot sptr[b / 32] + 32 t + b % 32, its block column at
+// bci[slot], its values in nine planes val[e * slots + slot] (e = 3 * row + column within
+// the block); blen[b] blocks per block row.
+template <class V>
+struct Sell3View {
+  int n = 0;              // scalar rows (3 nbr)
+  int nbr = 0;            // block rows
+  long long nblocks = 0;  // stored blocks (nnz / 9)
+  long long slots = 0;    // plane length (blocks plus slice padding)
+  const int *sptr = nullptr;
+  const int *blen = nullptr;
+  const int *bci = nullptr;
+  const V *val = nullptr;
+};
+// *d_flag |= 1 unless the CSR pattern (n rows) is 3x3-blocked as above; d_smax[s] (zeroed by
+// the caller, one per slice of 32 block rows) = the most blocks of a block row of slice s
+amg_status block3_detect(int n, const int *rp, const int *ci, int *d_flag, int *d_smax, cudaStream_t s);
+// The sliced layout from the CSR arrays: sptr (slice offsets, the scan of 32 d_smax), blen,
+// bci, the binary64 planes and (v32 != NULL) their binary32 copy
+amg_status block3_fill(int n, const int *rp, const int *ci, const double *val, const int *sptr, int *blen,
+                       int *bci, double *v64, float *v32, long long slots, cudaStream_t s);
+// r = b - A x, or with dinv != NULL r = b - A (D^{-1} b) (the residual after the first
+// l1-Jacobi sweep from zero; x unused)
+template <class V>
+amg_status block3_residual(const Sell3View<V> &A, const V *b, const V *x, const V *dinv, V *r, cudaStream_t s);
+// the residual above into r_scratch, then bc = P^T r
+template <class V>
+amg_status block3_resid_restrict(const Sell3View<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
+                                 const V *b, const V *x, const V *dinv, V *r_scratch, V *bc, cudaStream_t s);
+// spmv_dots_scalars on the 3x3-block layout (part holds 3 * part_blocks doubles)
+amg_status block3_spmv_dots(const Sell3View<double> &A, const double *w, const double *r, const double *q, double *v,
+                            double *part, int part_blocks, double *scal, unsigned *tick, int first, cudaStream_t s);
 
 // FCG device scalars (one array of doubles on the device).
 enum FcgSlot { kAlpha = 0, kBeta, kGamma, kRho, kRhoPrev, kCoef, kStep, kRR, kBB, kFlags, kFcgSlots };

@@ -272,6 +272,47 @@ def random_spd_hubs(n: int, avg_degree: float = 4.0, n_hubs: int = 8, hub_degree
                       np.concatenate([w, w, diag]))
 
 
+def random_block3_spd(nbr: int, avg_blocks: float = 6.0, n_hubs: int = 3, hub_blocks: int = 80, seed: int = 0,
+                      zero_frac: float = 0.1):
+    """Random s.p.d. matrix of 3 nbr rows whose pattern is made of whole 3x3 blocks (block rows
+    3b..3b+2 share their columns, in aligned triples), like a nodal 3D vector problem with
+    interleaved unknowns: off-diagonal blocks U[-1, 1] with a fraction zero_frac of their
+    entries exactly zero (stored), a few hub block rows far longer than the mean, and
+    diagonal blocks made strictly diagonally dominant.  Bit-symmetric."""
+    rng = np.random.default_rng(seed)
+    m = int(avg_blocks * nbr / 2)
+    a = rng.integers(0, nbr, size=m)
+    b = rng.integers(0, nbr, size=m)
+    hubs = rng.choice(nbr, size=n_hubs, replace=False)
+    a = np.concatenate([a, np.repeat(hubs, hub_blocks)])
+    b = np.concatenate([b, rng.integers(0, nbr, size=n_hubs * hub_blocks)])
+    keep = a != b
+    a, b = np.minimum(a[keep], b[keep]), np.maximum(a[keep], b[keep])
+    pairs = np.unique(a.astype(np.int64) * nbr + b)
+    a, b = pairs // nbr, pairs % nbr
+    blk = rng.uniform(-1.0, 1.0, size=(len(a), 3, 3))
+    blk[rng.random(blk.shape) < zero_frac] = 0.0
+    rows, cols, vals = [], [], []
+    ii, jj = np.meshgrid(np.arange(3), np.arange(3), indexing="ij")
+    for (x, y, B) in ((a, b, blk), (b, a, blk.transpose(0, 2, 1))):
+        rows.append((3 * x[:, None, None] + ii[None]).ravel())
+        cols.append((3 * y[:, None, None] + jj[None]).ravel())
+        vals.append(B.ravel())
+    n = 3 * nbr
+    r, c, v = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    rowsum = np.bincount(r, weights=np.abs(v), minlength=n)
+    D = rng.uniform(-0.2, 0.2, size=(nbr, 3, 3))
+    D = 0.5 * (D + D.transpose(0, 2, 1))
+    D[:, ii == jj] = 0.0
+    dsum = np.abs(D).sum(axis=2).ravel()
+    D[:, np.arange(3), np.arange(3)] = (rowsum + dsum + rng.uniform(0.1, 1.0, size=n)).reshape(nbr, 3)
+    d = np.arange(nbr)
+    r = np.concatenate([r, (3 * d[:, None, None] + ii[None]).ravel()])
+    c = np.concatenate([c, (3 * d[:, None, None] + jj[None]).ravel()])
+    v = np.concatenate([v, D.ravel()])
+    return _exact_csr(n, r, c, v)
+
+
 def smooth_vector_ones(n: int) -> np.ndarray:
     return np.ones(n, np.float64)
 

@@ -144,3 +144,22 @@ def test_elasticity_q1_full_size_counts():
     60,756,300 by the pair count above (both without building the matrix)."""
     assert 3 * 63 * 64 * 64 == 774144
     assert 9 * _nb(63) * _nb(64) ** 2 == 60756300
+
+
+def test_random_block3_spd_pattern():
+    """Block rows 3b..3b+2 share their columns, in aligned triples; hub block rows far longer
+    than the mean; stored zeros inside blocks; bit-symmetric and s.p.d."""
+    rp, ci, val = P.random_block3_spd(300, avg_blocks=5.0, n_hubs=2, hub_blocks=60, seed=3)
+    n = len(rp) - 1
+    assert n == 900
+    lens = np.diff(rp)
+    for b in range(n // 3):
+        r = [ci[rp[3 * b + i]:rp[3 * b + i + 1]] for i in range(3)]
+        assert np.array_equal(r[0], r[1]) and np.array_equal(r[0], r[2])
+        assert len(r[0]) % 3 == 0 and (r[0][0::3] % 3 == 0).all()
+        assert np.array_equal(r[0][1::3], r[0][0::3] + 1) and np.array_equal(r[0][2::3], r[0][0::3] + 2)
+    assert lens.max() >= 3 * 60 and lens.mean() < 3 * 10
+    assert (val == 0).sum() > 0
+    A = _dense((rp, ci, val))
+    assert np.array_equal(A, A.T)
+    np.linalg.cholesky(A)
