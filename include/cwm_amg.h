@@ -100,6 +100,14 @@ typedef struct {
                            level's residual in the V-cycle and the FCG's SpMV with its dot
                            products stream a copy of it in 3x3 blocks (one column index
                            per block; the same products summed in block order); -1 = never */
+  int sliced;           /* sliced copies (rows sorted by length within windows of 256,
+                           one or more lanes per row, the lanes of a warp reading
+                           consecutive words) streamed by the V-cycle on the levels that
+                           take the coarse correction and post-sweep through A P
+                           (coupled_post): 0 = auto (default: A P on such levels with at
+                           least 131072 rows and more than 16 entries per row on average,
+                           one lane per row), 1 = A and A P on every such level, lanes per
+                           row from the longest row, -1 = never */
 } amg_params;
 
 /* Statistics filled by amg_pcg_solve and amg_stats. */

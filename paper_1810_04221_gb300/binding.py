@@ -49,6 +49,7 @@ class AmgParams(C.Structure):
         ("galerkin_fp32_from", C.c_int),
         ("coupled_post", C.c_int),
         ("block3", C.c_int),
+        ("sliced", C.c_int),
     ]
 
 

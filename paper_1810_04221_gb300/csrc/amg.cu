@@ -19,6 +19,24 @@ using namespace cwm;
 
 namespace {
 
+// A sliced copy of a level operator or of its A P (sell.cu), in the V-cycle's precision.
+struct SellBuf {
+  int n = 0, lanes = 1;
+  long long nnz = 0, slots = 0;
+  DBuf<int> sptr, perm, len, col;
+  DBuf<double> v64;
+  DBuf<float> v32;
+  template <class V>
+  SellView<V> view(const V *values) const {
+    SellView<V> a;
+    if (!values) return a;
+    a.n = n; a.lanes = lanes; a.nnz = nnz; a.sptr = sptr.get(); a.perm = perm.get(); a.len = len.get();
+    a.col = col.get();
+    a.val = values;
+    return a;
+  }
+};
+
 struct Level {
   int n = 0;
   long long nnz = 0;
@@ -55,6 +73,8 @@ struct Level {
   DBuf<double> b3_val;
   DBuf<float> b3_val32;
   long long b3_slots = 0;
+  // sliced copies of A and of A P (levels with A P and long rows; see build_sell)
+  SellBuf sa, sap;
 
   template <class V>
   void split(CsrView<V> &a, bool fp64) const {
@@ -496,6 +516,85 @@ amg_status build_block3(amg_hierarchy *h) {
   return AMG_OK;
 }
 
+// Sliced copies (sell.cu) for the levels that take the coarse correction and post-sweep
+// through A P, in the V-cycle's precision.  sliced = 1: A and A P of every such level (A not
+// where the finest operator has its 3x3-block layout), lanes per row from the longest row.
+// sliced = 0 (auto): A P only, on such levels with at least kSellAutoMinRows rows and a mean
+// row longer than kApAutoMinMean, one lane per row.  Measured on Q1 elasticity 64^3
+// (binary32): the sliced A P took the coarse correction + post-sweep of level 0 (774K rows)
+// from 78.5 to 57 us and of level 1 (194K rows) from 47 to 29 us; the sliced residuals were
+// no faster than the CSR row blocks on level 1 (44-45 against 47 us) and slower on the
+// smaller levels, where a few long rows per warp leave the kernel latency-bound (level 2:
+// 25 against 18 us; levels 3-4: 14-18 against 8-10 us), and several lanes per row cost
+// level 0's A P 8 us.  Every matrix is planned first (sorted windows, slice lengths and
+// their scan), then one synchronisation reads the slot counts, then the copies are filled.
+constexpr int kSellAutoMinRows = 131072;
+amg_status build_sell(amg_hierarchy *h) {
+  const amg_params &P = h->prm;
+  if (P.sliced < 0) return AMG_OK;
+  cudaStream_t s = h->stream;
+  const bool f32 = P.vcycle_fp32 != 0;
+  struct Job {
+    int k;
+    bool is_ap;
+  };
+  std::vector<Job> jobs;
+  for (int k = 0; k + 1 < (int)h->lev.size(); ++k) {
+    Level &L = h->lev[k];
+    if (L.ap_nnz <= 0 || !L.ap_val.get()) continue;
+    if (P.sliced == 0 && ((double)L.nnz <= kApAutoMinMean * L.n || L.n < kSellAutoMinRows)) continue;
+    // slot offsets are int32: skip a matrix whose padded layout could exceed them (at most
+    // 32 slots per row and step)
+    const long long n32 = ((long long)L.n + 31) / 32 * 32;
+    if (P.sliced == 1 && !(k == 0 && L.b3_val.get()) && n32 * (L.max_row + 32) < (long long)INT32_MAX)
+      jobs.push_back({k, false});
+    if (n32 * (L.ap_max_row + 32) < (long long)INT32_MAX) jobs.push_back({k, true});
+  }
+  if (jobs.empty()) return AMG_OK;
+  int nmax = 0;
+  for (const Job &j : jobs) nmax = std::max(nmax, h->lev[j.k].n);
+  DBuf<int> slen, scan, totals;
+  CWM_TRY(slen.alloc((size_t)nmax + 1, s));
+  CWM_TRY(scan.alloc(scan_scratch_ints((long long)nmax + 1), s));
+  CWM_TRY(totals.alloc(jobs.size(), s));
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    Level &L = h->lev[jobs[q].k];
+    LevelTag tag(jobs[q].k);
+    SellBuf &S = jobs[q].is_ap ? L.sap : L.sa;
+    const int *rp = jobs[q].is_ap ? L.ap_rp.get() : L.rp.get();
+    S.lanes = P.sliced == 1 ? sell_lanes(jobs[q].is_ap ? L.ap_max_row : L.max_row) : 1;
+    const int ns = sell_slices(L.n, S.lanes);
+    CWM_TRY(S.perm.alloc(L.n, s));
+    CWM_TRY(S.len.alloc(L.n, s));
+    CWM_TRY(S.sptr.alloc((size_t)ns + 1, s));
+    CWM_TRY(sell_plan(L.n, S.lanes, rp, S.perm.get(), S.len.get(), slen.get(), S.sptr.get(), scan.get(), s));
+    CWM_CUDA(cudaMemcpyAsync(totals.get() + q, S.sptr.get() + ns, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  }
+  std::vector<int> tot(jobs.size());
+  CWM_CUDA(cudaMemcpyAsync(tot.data(), totals.get(), sizeof(int) * jobs.size(), cudaMemcpyDeviceToHost, s));
+  CWM_TRY(read_err(h, "amg_setup (sliced copies)"));  // synchronises
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    Level &L = h->lev[jobs[q].k];
+    LevelTag tag(jobs[q].k);
+    SellBuf &S = jobs[q].is_ap ? L.sap : L.sa;
+    S.n = L.n;
+    S.nnz = jobs[q].is_ap ? L.ap_nnz : L.nnz;
+    S.slots = tot[q];
+    const int *rp = jobs[q].is_ap ? L.ap_rp.get() : L.rp.get();
+    const int *ci = jobs[q].is_ap ? L.ap_ci.get() : L.ci.get();
+    const double *val = jobs[q].is_ap ? L.ap_val.get() : L.val.get();
+    CWM_TRY(S.col.alloc((size_t)S.slots, s));
+    if (f32) {
+      CWM_TRY(S.v32.alloc((size_t)S.slots, s));
+      CWM_TRY(sell_fill<float>(L.n, rp, ci, val, S.view<float>(S.v32.get()), S.col.get(), S.v32.get(), s));
+    } else {
+      CWM_TRY(S.v64.alloc((size_t)S.slots, s));
+      CWM_TRY(sell_fill<double>(L.n, rp, ci, val, S.view<double>(S.v64.get()), S.col.get(), S.v64.get(), s));
+    }
+  }
+  return AMG_OK;
+}
+
 amg_status finish_level(amg_hierarchy *h, Level &L) {
   cudaStream_t s = h->stream;
   {  // the long rows of a sub-warp-tile level (see long_row_min)
@@ -561,6 +660,8 @@ struct LevelVec<double> {
   static bool has_ap(const Level &L) { return L.ap_nnz > 0 && L.ap_val.get(); }
   static CsrView<double> AP(const Level &L) { return L.ap_view<double>(L.ap_val.get()); }
   static Sell3View<double> B3(const Level &L) { return L.block3_view<double>(L.b3_val.get()); }
+  static SellView<double> SA(const Level &L) { return L.sa.view<double>(L.sa.v64.get()); }
+  static SellView<double> SAP(const Level &L) { return L.sap.view<double>(L.sap.v64.get()); }
 };
 template <>
 struct LevelVec<float> {
@@ -575,6 +676,8 @@ struct LevelVec<float> {
   static bool has_ap(const Level &L) { return L.ap_nnz > 0 && L.ap_val32.get(); }
   static CsrView<float> AP(const Level &L) { return L.ap_view<float>(L.ap_val32.get()); }
   static Sell3View<float> B3(const Level &L) { return L.block3_view<float>(L.b3_val32.get()); }
+  static SellView<float> SA(const Level &L) { return L.sa.view<float>(L.sa.v32.get()); }
+  static SellView<float> SAP(const Level &L) { return L.sap.view<float>(L.sap.v32.get()); }
 };
 
 template <>
@@ -689,15 +792,23 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   // level with A P (built for the levels that skip the fused kernels, or for every level with
   // coupled_post = 1) takes the coarse correction and the post-sweep through it instead.
   const bool ap = h->prm.post_sweeps == 1 && LV::has_ap(L);
-  // the finest operator in 3x3 blocks: the residual streams the block layout
+  // the finest operator in 3x3 blocks, or sliced copies of A and A P: the residual and the
+  // coarse correction + post-sweep stream those layouts
   const Sell3View<V> B3 = k == 0 ? LV::B3(L) : Sell3View<V>{};
-  if (B3.nbr > 0 && ap && zero_init && h->prm.pre_sweeps == 1) {
+  const SellView<V> SA = LV::SA(L), SAP = LV::SAP(L);
+  if ((B3.nbr > 0 || SA.n > 0) && ap && zero_init && h->prm.pre_sweeps == 1) {
     // the first sweep from zero, xs = D^{-1} b, formed on the fly inside the residual
     // r = b - A xs and inside the coarse correction + post-sweep through A P
     Level &C = h->lev[k + 1];
-    CWM_TRY(block3_resid_restrict<V>(B3, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, nullptr, dinv, t1,
+    if (B3.nbr > 0)
+      CWM_TRY(block3_resid_restrict<V>(B3, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, nullptr, dinv, t1,
+                                       LV::b(C), s));
+    else
+      CWM_TRY(sell_resid_restrict<V>(SA, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, nullptr, dinv, t1,
                                      LV::b(C), s));
     for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C), LV::x(C), g == 0));
+    if (SAP.n > 0)
+      return sell_prolong_jacobi_ap<V>(SAP, C.n, dinv, t1, L.agg.get(), LV::p(L), LV::x(C), b, true, x, s);
     return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, t1, L.agg.get(), LV::p(L), LV::x(C), b, true, x, s);
   }
   if (!ap && B3.nbr == 0 && zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 &&
@@ -719,10 +830,15 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   if (B3.nbr > 0 && xs)
     CWM_TRY(block3_resid_restrict<V>(B3, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, nullptr, rtmp, LV::b(C),
                                      s));
+  else if (SA.n > 0 && xs)
+    CWM_TRY(sell_resid_restrict<V>(SA, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, nullptr, rtmp, LV::b(C),
+                                   s));
   else
     CWM_TRY(resid_restrict_rb<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, xs, rtmp, LV::b(C), s));
   for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C), LV::x(C), g == 0));
-  if (ap)  // rtmp still holds b - A xs
+  if (ap && SAP.n > 0)  // rtmp still holds b - A xs
+    return sell_prolong_jacobi_ap<V>(SAP, C.n, dinv, rtmp, L.agg.get(), LV::p(L), LV::x(C), xs, false, x, s);
+  if (ap)
     return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, rtmp, L.agg.get(), LV::p(L), LV::x(C), xs, false, x, s);
   V *y = (xs == t1) ? t2 : t1;
   CWM_TRY(prolong<V>(A.n, L.agg.get(), LV::p(L), LV::x(C), xs, y, s));
@@ -781,6 +897,7 @@ void amg_default_params(amg_params *p) {
   p->galerkin_fp32_from = 0;
   p->coupled_post = 0;
   p->block3 = 0;
+  p->sliced = 0;
 }
 
 const char *amg_status_string(amg_status s) {
@@ -824,7 +941,7 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   }
   if (P.sweeps_per_level < 1 || P.sweeps_per_level > kMaxSweeps || P.max_levels < 1 || P.pre_sweeps < 0 ||
       P.post_sweeps < 0 || P.coarse_sweeps < 0 || P.coarse_max < 0 || P.galerkin_fp32_from < 0 ||
-      P.coupled_post < -1 || P.coupled_post > 1) {
+      P.coupled_post < -1 || P.coupled_post > 1 || P.block3 < -1 || P.block3 > 0 || P.sliced < -1 || P.sliced > 1) {
     set_error("amg_setup: parameter out of range");
     return AMG_ERR_INVALID_ARG;
   }
@@ -909,6 +1026,7 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
     }
   }
   CWM_TRY(build_ap(h));
+  CWM_TRY(build_sell(h));
   // FCG work vectors
   CWM_TRY(h->r.alloc(n, s));
   CWM_TRY(h->w.alloc(n, s));

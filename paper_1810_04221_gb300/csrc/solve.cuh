@@ -168,6 +168,46 @@ amg_status block3_residual(const Sell3View<V> &A, const V *b, const V *x, const 
 template <class V>
 amg_status block3_resid_restrict(const Sell3View<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                                  const V *b, const V *x, const V *dinv, V *r_scratch, V *bc, cudaStream_t s);
+// ---------------------------------------------------------------- sliced rows ----
+// A long-row operator (or A P) in sliced ELL (sell.cu): rows sorted by length, longest
+// first, within windows of 256 rows (perm[p] = the row at position p, len[p] its length);
+// `lanes` (K) lanes per row, R = 32 / K positions per slice; entry e of position p = R s + r
+// at slot sptr[s] + 32 (e / K) + K r + e % K (col, val).
+template <class V>
+struct SellView {
+  int n = 0;          // rows (0: no sliced copy)
+  int lanes = 1;      // K
+  long long nnz = 0;  // stored entries
+  const int *sptr = nullptr;
+  const int *perm = nullptr;
+  const int *len = nullptr;
+  const int *col = nullptr;
+  const V *val = nullptr;
+};
+// Lanes per row for rows of at most max_row entries (no lane walks more than ~24), and the
+// number of slices of n rows
+int sell_lanes(int max_row);
+int sell_slices(int n, int K);
+// perm, len (n ints each), slen (one slice length per slice, scratch) and sptr (their
+// exclusive scan, sell_slices(n, K) + 1 ints; sptr[last] = the slots to allocate)
+amg_status sell_plan(int n, int K, const int *rp, int *perm, int *len, int *slen, int *sptr, int *scan_scratch,
+                     cudaStream_t s);
+// col and sval (sptr[last] slots each) from the CSR arrays, values rounded to V
+template <class V>
+amg_status sell_fill(int n, const int *rp, const int *ci, const double *val, const SellView<V> &S, int *col,
+                     V *sval, cudaStream_t s);
+// r = b - A x, or with dinv != NULL r = b - A (D^{-1} b) (x unused)
+template <class V>
+amg_status sell_residual(const SellView<V> &A, const V *b, const V *x, const V *dinv, V *r, cudaStream_t s);
+// the residual above into r_scratch, then bc = P^T r
+template <class V>
+amg_status sell_resid_restrict(const SellView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
+                               const V *b, const V *x, const V *dinv, V *r_scratch, V *bc, cudaStream_t s);
+// prolong_jacobi_ap on the sliced A P
+template <class V>
+amg_status sell_prolong_jacobi_ap(const SellView<V> &AP, int nc, const V *dinv, const V *r, const int *agg,
+                                  const V *p, const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s);
+
 // spmv_dots_scalars on the 3x3-block layout (part holds 3 * part_blocks doubles)
 amg_status block3_spmv_dots(const Sell3View<double> &A, const double *w, const double *r, const double *q, double *v,
                             double *part, int part_blocks, double *scal, unsigned *tick, int first, cudaStream_t s);

@@ -55,7 +55,7 @@ def test_library_loads_and_host_calls_work(lib_path):
     # the remaining documented defaults
     assert (p.vcycle_fp32, p.check_input, p.keep_sweeps, p.loop_cap, p.trace) == (0, 1, 0, 0, 0)
     assert (p.tail_rows, p.stall_ratio, p.gamma, p.galerkin_fp32_from, p.coupled_post) == (-1, 0.0, 1, 0, 0)
-    assert p.block3 == 0
+    assert (p.block3, p.sliced) == (0, 0)
     assert binding.status_name(binding.AMG_ERR_NOT_SPD) == "AMG_ERR_NOT_SPD"
     # argument checks happen before any device work
     lib.amg_num_levels.restype = C.c_int
