@@ -26,6 +26,22 @@ namespace cwm {
 constexpr int kS3 = 32;           // block rows per slice (one warp)
 constexpr int kS3Block = 128;     // threads per block of the residual kernels
 constexpr int kS3DotsBlock = 256; // threads per block of the SpMV + dots kernel (block_sums layout)
+// Resident blocks per SM that the SpMV + dots kernel's registers must allow, and blocks per
+// step.  Measured on Q1 elasticity 64^3 (average per launch over a solve): 2 blocks and 2 per
+// step (116 registers, a fifth of the warp slots, FP64 pipe 75% busy) 145 us; 3 blocks and
+// 1 per step (80 registers) 155 us; 4 and 1 (64 registers) 156 us -- the FP64-issue-bound
+// chains want independent FMAs more than warps.
+#ifndef CWM_B3_DOTS_MIN_BLOCKS
+#define CWM_B3_DOTS_MIN_BLOCKS 2
+#endif
+#ifndef CWM_B3_DOTS_UNROLL
+#define CWM_B3_DOTS_UNROLL 2
+#endif
+// Blocks per step of the binary32 residual (binary64 takes 2): 4 measured 54.5 us against
+// 59.6 us with 2 (Q1 elasticity 64^3, level 0).
+#ifndef CWM_B3_RESID_UNROLL32
+#define CWM_B3_RESID_UNROLL32 4
+#endif
 
 // ------------------------------------------------------------ detection ----
 // A warp per block row.  flag |= 1 when rows 3b..3b+2 differ in length or columns, or a
@@ -118,56 +134,42 @@ amg_status block3_fill(int n, const int *rp, const int *ci, const double *val, c
 
 // ------------------------------------------------------------ row products ----
 // The three rows of block row b against x: acc[i] = init[i] - sum over the row's blocks of
-// a_(3b+i, 3c+j) x_(3c+j) (NEG) or + (otherwise).  X_SCALED reads x_j = d_j * x_j on the fly
-// (the first l1-Jacobi sweep from zero, x = D^{-1} b).  Two blocks per step, their loads
+// a_(3b+i, 3c+j) x_(3c+j) (NEG) or + (otherwise).  SCALED reads x_j = d_j * x_j on the fly
+// (the first l1-Jacobi sweep from zero, x = D^{-1} b).  UB blocks per step, their loads
 // issued before the FMAs.
-template <class V, bool NEG, bool SCALED>
+template <class V, bool NEG, bool SCALED, int UB>
 __device__ __forceinline__ void block3_rows(const Sell3View<V> &A, long long base, int len, int tmax,
                                             const V *__restrict__ x, const V *__restrict__ d, V (&acc)[3]) {
   const long long P = A.slots;
   const V sg = NEG ? V(-1) : V(1);
-  int t = 0;
-  for (; t + 1 < tmax; t += 2) {
-    const bool l0 = t < len, l1 = t + 1 < len;
-    const long long q0 = base + (long long)t * kS3, q1 = q0 + kS3;
-    const int c0 = l0 ? __ldcs(A.bci + q0) : 0, c1 = l1 ? __ldcs(A.bci + q1) : 0;
-    V a0[9], a1[9], x0[3], x1[3];
+  for (int t = 0; t < tmax; t += UB) {
+    int c[UB];
+    V a[UB][9], xv[UB][3];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      a0[e] = l0 ? __ldcs(A.val + e * P + q0) : V(0);
-      a1[e] = l1 ? __ldcs(A.val + e * P + q1) : V(0);
+    for (int u = 0; u < UB; ++u) {
+      const bool live = t + u < len;
+      const long long q = base + (long long)(t + u) * kS3;
+      c[u] = live ? __ldcs(A.bci + q) : 0;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) a[u][e] = live ? __ldcs(A.val + e * P + q) : V(0);
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      x0[j] = l0 ? (SCALED ? __ldg(d + 3 * c0 + j) * __ldg(x + 3 * c0 + j) : __ldg(x + 3 * c0 + j)) : V(0);
-      x1[j] = l1 ? (SCALED ? __ldg(d + 3 * c1 + j) * __ldg(x + 3 * c1 + j) : __ldg(x + 3 * c1 + j)) : V(0);
+    for (int u = 0; u < UB; ++u) {
+      const bool live = t + u < len;
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj)
+        xv[u][jj] = live ? (SCALED ? __ldg(d + 3 * c[u] + jj) * __ldg(x + 3 * c[u] + jj) : __ldg(x + 3 * c[u] + jj))
+                         : V(0);
     }
-    if (l0) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+    for (int u = 0; u < UB; ++u) {
+      if (t + u < len) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) acc[i] = fma(sg * a0[3 * i + j], x0[j], acc[i]);
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) acc[i] = fma(sg * a[u][3 * i + jj], xv[u][jj], acc[i]);
+      }
     }
-    if (l1) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) acc[i] = fma(sg * a1[3 * i + j], x1[j], acc[i]);
-    }
-  }
-  if (t < tmax && t < len) {
-    const long long q0 = base + (long long)t * kS3;
-    const int c0 = __ldcs(A.bci + q0);
-    V a0[9], x0[3];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) a0[e] = __ldcs(A.val + e * P + q0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      x0[j] = SCALED ? __ldg(d + 3 * c0 + j) * __ldg(x + 3 * c0 + j) : __ldg(x + 3 * c0 + j);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) acc[i] = fma(sg * a0[3 * i + j], x0[j], acc[i]);
   }
 }
 
@@ -189,7 +191,8 @@ __global__ void __launch_bounds__(kS3Block) k_block3_resid(Sell3View<V> A, const
   V acc[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) acc[i] = in ? b[3 * br + i] : V(0);
-  block3_rows<V, true, SCALED>(A, s0 + lane, len, tmax, SCALED ? b : x, d, acc);
+  block3_rows<V, true, SCALED, sizeof(V) == 4 ? CWM_B3_RESID_UNROLL32 : 2>(A, s0 + lane, len, tmax, SCALED ? b : x, d,
+                                                                            acc);
   if (in) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) r[3 * br + i] = acc[i];
@@ -221,7 +224,7 @@ amg_status block3_resid_restrict(const Sell3View<V> &A, int nc, const int *mptr,
 // v = A w with the partial sums of w.r, w.v and w.q (q may be NULL) of Algorithm 3; the
 // last block turns every block's partials into the FCG scalars (fcg_scalars_from).  A block
 // of 256 threads takes 8 slices at a time, grid-stride.
-__global__ void __launch_bounds__(kS3DotsBlock)
+__global__ void __launch_bounds__(kS3DotsBlock, CWM_B3_DOTS_MIN_BLOCKS)
     k_block3_spmv_dots(Sell3View<double> A, const double *__restrict__ w, const double *__restrict__ r,
                        const double *__restrict__ q, double *__restrict__ v, double *__restrict__ part, double *scal,
                        unsigned *tick, int first) {
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(kS3DotsBlock)
       qi[i] = (in && q) ? q[3 * br + i] : 0.0;
     }
     double acc[3] = {0.0, 0.0, 0.0};
-    block3_rows<double, false, false>(A, s0 + lane, len, tmax, w, nullptr, acc);
+    block3_rows<double, false, false, CWM_B3_DOTS_UNROLL>(A, s0 + lane, len, tmax, w, nullptr, acc);
     if (in) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) {

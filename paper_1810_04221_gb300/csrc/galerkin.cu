@@ -73,6 +73,13 @@ struct Arith<float> {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
 };
 
+// Acc(0) + t without an FP operation: t itself, except -0 which becomes +0 (the sum of a
+// run starts from +0.0).  FP64 instructions issue at a low rate on GB300.
+__device__ __forceinline__ double plus_zero(double t) {
+  return (unsigned long long)__double_as_longlong(t) == 0x8000000000000000ull ? 0.0 : t;
+}
+__device__ __forceinline__ float plus_zero(float t) { return __float_as_uint(t) == 0x80000000u ? 0.0f : t; }
+
 // t_ij = (p_i p_j) a_ij in the accumulation type
 template <class Acc>
 __device__ __forceinline__ Acc term(double pi, double pj, double a) {
@@ -122,9 +129,9 @@ __device__ __forceinline__ double run_value(const RowSrc &r, const unsigned long
       }
     }
   }
-  Acc sum = Acc(0);
+  Acc sum = plus_zero(t[0]);
 #pragma unroll
-  for (int e = 0; e < 4; ++e)
+  for (int e = 1; e < 4; ++e)
     if (e < len) sum = Arith<Acc>::add(sum, t[e]);
   return (double)sum;
 }
@@ -216,9 +223,9 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
       }
     }
   }
-  Acc acc = Acc(0);
+  Acc acc = plus_zero(tm[0]);
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
+  for (int m = 1; m < 4; ++m)
     if (m < len) acc = Arith<Acc>::add(acc, tm[m]);
   const double sum = (double)acc;
   const int out = rpc[I] + rank;
@@ -278,38 +285,76 @@ __device__ __forceinline__ void sort_row_keys(const RowSrc &r, int L, unsigned l
 }
 
 // A coarse row with 32 < L <= kWarpCap entries: keys (J, slot) sorted by the warp in
-// registers (bitonic), runs of equal J summed in canonical order.
+// registers (bitonic), then two passes over the sorted positions.  Pass 1, every lane: the
+// term t = (p_i p_j) a_ij of each position, its canonical key (min(i,j), max(i,j), i) packed in
+// 64 bits (into keys[], whose (J, slot) is no longer needed) and its J (jq[]).  Pass 2, the
+// first position of each run of equal J: orders the run's (at most four) terms by their
+// canonical keys and sums them.  The FP64 products then run on full warps; only the few
+// additions of each run run on its first lane.
 template <class Acc>
-__device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsigned long long *keys,
-                                                  const int *__restrict__ ci, const double *__restrict__ val,
-                                                  const int *__restrict__ agg, const double *__restrict__ p,
-                                                  int *__restrict__ cnt, const int *__restrict__ rpc,
-                                                  int *__restrict__ cic, double *__restrict__ valc,
-                                                  double *__restrict__ diag_c, int *err) {
+__device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsigned long long *keys, double *tq,
+                                                  unsigned *jq, const int *__restrict__ ci,
+                                                  const double *__restrict__ val, const int *__restrict__ agg,
+                                                  const double *__restrict__ p, int *__restrict__ cnt,
+                                                  const int *__restrict__ rpc, int *__restrict__ cic,
+                                                  double *__restrict__ valc, double *__restrict__ diag_c, int *err) {
   const int lane = threadIdx.x & 31;
   const int L = r.L1 + r.L2;
   if (L <= 64) sort_row_keys<2>(r, L, keys, ci, agg, lane);
   else if (L <= 128) sort_row_keys<4>(r, L, keys, ci, agg, lane);
   else sort_row_keys<8>(r, L, keys, ci, agg, lane);
+  for (int q = lane; q < L; q += 32) {
+    const unsigned long long key = keys[q];
+    const int local = (int)(key & 0xffffffffu);
+    const bool first = local < r.L1;
+    const int i = first ? r.i1 : r.i2;
+    const int k = first ? r.s1 + local : r.s2 + (local - r.L1);
+    const int j = ci[k];
+    tq[q] = (double)term<Acc>(p[i], p[j], val[k]);
+    jq[q] = (unsigned)(key >> 32);
+    const unsigned long long lo = (unsigned)min(i, j), hi = (unsigned)max(i, j);
+    keys[q] = (lo << 33) | (hi << 1) | (unsigned long long)(i == max(i, j) && i != j);
+  }
+  __syncwarp();
   int base = 0;
   for (int q0 = 0; q0 < L; q0 += 32) {
     const int q = q0 + lane;
     bool head = false;
     unsigned J = 0;
     if (q < L) {
-      J = (unsigned)(keys[q] >> 32);
-      head = q == 0 || (unsigned)(keys[q - 1] >> 32) != J;
+      J = jq[q];
+      head = q == 0 || jq[q - 1] != J;
     }
     const unsigned ball = __ballot_sync(0xffffffffu, head);
     if (head) {
       int len = 1;
-      while (len < 5 && q + len < L && (unsigned)(keys[q + len] >> 32) == J) ++len;
+      while (len < 5 && q + len < L && jq[q + len] == J) ++len;
       if (len > 4) { atomicOr(err, kErrInvalid); len = 4; }
-      const double s = run_value<Acc>(r, keys, q, len, ci, val, p);
+      unsigned long long ck[4];
+      Acc t[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ck[e] = e < len ? keys[q + e] : ~0ull;
+        t[e] = e < len ? (Acc)tq[q + e] : Acc(0);
+      }
+#pragma unroll
+      for (int a = 1; a < 4; ++a) {
+#pragma unroll
+        for (int b = a; b > 0; --b) {
+          if (ck[b] < ck[b - 1]) {
+            const unsigned long long x = ck[b]; ck[b] = ck[b - 1]; ck[b - 1] = x;
+            const Acc y = t[b]; t[b] = t[b - 1]; t[b - 1] = y;
+          }
+        }
+      }
+      Acc sum = plus_zero(t[0]);
+#pragma unroll
+      for (int e = 1; e < 4; ++e)
+        if (e < len) sum = Arith<Acc>::add(sum, t[e]);
       const int out = rpc[I] + base + __popc(ball & ((1u << lane) - 1u));
       cic[out] = (int)J;
-      valc[out] = s;
-      if ((int)J == I && diag_c) diag_c[I] = s;
+      valc[out] = (double)sum;
+      if ((int)J == I && diag_c) diag_c[I] = (double)sum;
     }
     base += __popc(ball);
   }
@@ -333,9 +378,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                     const int *__restrict__ rpc, int *__restrict__ cic, double *__restrict__ valc,
                     double *__restrict__ diag_c, int *__restrict__ long_rows, int *__restrict__ n_long, int *err) {
   __shared__ unsigned long long sbuf[kWarpsPerBlock][kWarpCap];
+  __shared__ double stq[kWarpsPerBlock][kWarpCap];
+  __shared__ unsigned sjq[kWarpsPerBlock][kWarpCap];
   const int lane = threadIdx.x & 31;
   const int half = lane >> 4;
   unsigned long long *keys = sbuf[threadIdx.x >> 5];
+  double *tq = stq[threadIdx.x >> 5];
+  unsigned *jq = sjq[threadIdx.x >> 5];
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long base = warp0 * 2; base < nc; base += nwarps * 2) {
@@ -362,7 +411,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       if (L <= 32) {
         galerkin_row_reg<Acc>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (L <= kWarpCap) {
-        galerkin_row_smem<Acc>(r, I, keys, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+        galerkin_row_smem<Acc>(r, I, keys, tq, jq, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (long_rows && lane == 0) {
         long_rows[atomicAdd(n_long, 1)] = I;
       }

@@ -20,6 +20,12 @@
 namespace cwm {
 
 constexpr int kSellWin = 256;  // rows sorted together (one block)
+// Entries per lane whose loads are in flight together in binary32 (4 in binary64): 16
+// measured 59.1 / 31.0 us on Q1 elasticity 64^3 levels 0 / 1 (A P), 8 gave 60.8 / 31.6, 4
+// gave 61.1 / 32.1.
+#ifndef CWM_SELL_UNROLL32
+#define CWM_SELL_UNROLL32 16
+#endif
 constexpr int kSellBlock = 128;
 
 // Window w's rows sorted by (length descending, index ascending): perm and len per position.
@@ -107,26 +113,28 @@ amg_status sell_fill(int n, const int *rp, const int *ci, const double *val, con
 }
 
 // The K lanes of one row (all 32 lanes of the warp call this together): lane j sums
-// -val x[col] over the row's entries e = j, j + K, ... (four entries' loads in flight), the
-// K partial sums are added by shuffles and init joins them; every lane returns the total.
+// -val x[col] over the row's entries e = j, j + K, ... (U entries' loads in flight:
+// CWM_SELL_UNROLL32 in binary32, 4 in binary64), the K partial sums are added
+// by shuffles and init joins them; every lane returns the total.
 template <class V, int K, bool SCALED>
 __device__ __forceinline__ V sell_row(const SellView<V> &A, long long base, int L, int j, const V *__restrict__ x,
                                       const V *__restrict__ d, V init) {
+  constexpr int U = sizeof(V) == 4 ? CWM_SELL_UNROLL32 : 4;
   V acc = V(0);
   const int steps = L > j ? (L - j + K - 1) / K : 0;  // this lane's entries
   int t = 0;
-  for (; t + 4 <= steps; t += 4) {
-    int c[4];
-    V a[4], xv[4];
+  for (; t + U <= steps; t += U) {
+    int c[U];
+    V a[U], xv[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       c[u] = __ldcs(A.col + base + 32LL * (t + u));
       a[u] = __ldcs(A.val + base + 32LL * (t + u));
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) xv[u] = SCALED ? __ldg(d + c[u]) * __ldg(x + c[u]) : __ldg(x + c[u]);
+    for (int u = 0; u < U; ++u) xv[u] = SCALED ? __ldg(d + c[u]) * __ldg(x + c[u]) : __ldg(x + c[u]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc = fma(-a[u], xv[u], acc);
+    for (int u = 0; u < U; ++u) acc = fma(-a[u], xv[u], acc);
   }
   for (; t < steps; ++t) {
     const int c = __ldcs(A.col + base + 32LL * t);
