@@ -181,6 +181,10 @@ struct amg_hierarchy {
   TailArgs<float> tail32{};
   DBuf<unsigned> bar;   // grid-barrier state (count, generation)
   DBuf<unsigned char> tail_dev;  // device copies of tail64 and tail32
+  // float32 cycle: where the finest level's last kernel also writes its result in binary64
+  // (set by apply_vcycle; cycle_level reports in out64_written whether it did)
+  double *out64 = nullptr;
+  bool out64_written = false;
   void drop_graphs() {
     for (int g = 0; g < 2; ++g) {
       if (gexec[g]) cudaGraphExecDestroy(gexec[g]);
@@ -796,20 +800,26 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   // coarse correction + post-sweep stream those layouts
   const Sell3View<V> B3 = k == 0 ? LV::B3(L) : Sell3View<V>{};
   const SellView<V> SA = LV::SA(L), SAP = LV::SAP(L);
-  if ((B3.nbr > 0 || SA.n > 0) && ap && zero_init && h->prm.pre_sweeps == 1) {
+  if (ap && zero_init && h->prm.pre_sweeps == 1 && (B3.nbr > 0 || SA.n > 0 || A.n <= fuse_max_rows<V>())) {
     // the first sweep from zero, xs = D^{-1} b, formed on the fly inside the residual
-    // r = b - A xs and inside the coarse correction + post-sweep through A P
+    // r = b - A xs and inside the coarse correction + post-sweep through A P (no separate
+    // scale pass; in FP64 on CSR only up to the fused-kernel size limit, where the extra
+    // multiply per nonzero costs less than the pass)
     Level &C = h->lev[k + 1];
     if (B3.nbr > 0)
       CWM_TRY(block3_resid_restrict<V>(B3, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, nullptr, dinv, t1,
                                        LV::b(C), s));
-    else
+    else if (SA.n > 0)
       CWM_TRY(sell_resid_restrict<V>(SA, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), b, nullptr, dinv, t1,
                                      LV::b(C), s));
+    else
+      CWM_TRY(resid_scaled_restrict<V>(A, C.n, L.mptr.get(), L.mlist.get(), LV::p(L), dinv, b, t1, LV::b(C), s));
     for (int g = 0; g < gamma; ++g) CWM_TRY(cycle_level<V>(h, k + 1, LV::b(C), LV::x(C), g == 0));
+    double *x64 = (k == 0 && sizeof(V) == 4) ? h->out64 : nullptr;
+    if (x64) h->out64_written = true;
     if (SAP.n > 0)
-      return sell_prolong_jacobi_ap<V>(SAP, C.n, dinv, t1, L.agg.get(), LV::p(L), LV::x(C), b, true, x, s);
-    return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, t1, L.agg.get(), LV::p(L), LV::x(C), b, true, x, s);
+      return sell_prolong_jacobi_ap<V>(SAP, C.n, dinv, t1, L.agg.get(), LV::p(L), LV::x(C), b, true, x, s, x64);
+    return prolong_jacobi_ap<V>(LV::AP(L), C.n, dinv, t1, L.agg.get(), LV::p(L), LV::x(C), b, true, x, s, x64);
   }
   if (!ap && B3.nbr == 0 && zero_init && h->prm.pre_sweeps == 1 && h->prm.post_sweeps == 1 &&
       A.n <= fuse_max_rows<V>() && A.rb) {
@@ -856,11 +866,19 @@ amg_status cycle_level(amg_hierarchy *h, int k, const V *b, V *x, bool zero_init
   return AMG_OK;
 }
 
-amg_status apply_vcycle(amg_hierarchy *h, const double *r, double *w) {
+// w = B(r).  float32 cycle: r32_ready says that the finest level's float input already holds
+// r rounded to binary32 (written by the FCG update); the result comes back in binary64
+// from the finest level's last kernel where it can write it, else from a conversion pass.
+amg_status apply_vcycle(amg_hierarchy *h, const double *r, double *w, bool r32_ready = false) {
   if (!h->prm.vcycle_fp32) return vcycle_level<double>(h, 0, r, w);
   Level &L0 = h->lev[0];
-  CWM_TRY(to_float(L0.n, r, L0.b32.get(), h->stream));
-  CWM_TRY(vcycle_level<float>(h, 0, L0.b32.get(), L0.x32.get()));
+  if (!r32_ready) CWM_TRY(to_float(L0.n, r, L0.b32.get(), h->stream));
+  h->out64 = w;
+  h->out64_written = false;
+  const amg_status st = vcycle_level<float>(h, 0, L0.b32.get(), L0.x32.get());
+  h->out64 = nullptr;
+  CWM_TRY(st);
+  if (h->out64_written) return AMG_OK;
   return to_double(L0.n, L0.x32.get(), w, h->stream);
 }
 
@@ -1191,7 +1209,9 @@ amg_status fcg_iteration(amg_hierarchy *h, double *d_x, int first) {
   const Level &L0 = h->lev[0];
   const CsrView<double> A = L0.view64();
   double *scal = h->scal.get();
-  CWM_TRY(apply_vcycle(h, h->r.get(), h->w.get()));
+  // the float32 cycle's input: r in binary32, written by the previous iteration's update
+  const bool f32 = h->prm.vcycle_fp32 != 0;
+  CWM_TRY(apply_vcycle(h, h->r.get(), h->w.get(), f32 && !first));
   const Sell3View<double> B3 = LevelVec<double>::B3(L0);
   if (B3.nbr > 0)
     CWM_TRY(block3_spmv_dots(B3, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
@@ -1199,7 +1219,8 @@ amg_status fcg_iteration(amg_hierarchy *h, double *d_x, int first) {
   else
     CWM_TRY(spmv_dots_scalars(A, h->w.get(), h->r.get(), first ? nullptr : h->q.get(), h->vv.get(), h->part.get(),
                               scal, h->tick.get(), first, s));
-  CWM_TRY(fcg_update(L0.n, h->w.get(), h->vv.get(), h->d.get(), h->q.get(), d_x, h->r.get(), scal, h->part2.get(),
+  CWM_TRY(fcg_update(L0.n, h->w.get(), h->vv.get(), h->d.get(), h->q.get(), d_x, h->r.get(),
+                     f32 ? h->lev[0].b32.get() : nullptr, scal, h->part2.get(),
                      h->tick.get() + 1, first, s));
   CWM_CUDA(cudaMemcpyAsync(h->box.dbls, scal, sizeof(double) * kFcgSlots, cudaMemcpyDeviceToHost, s));
   CWM_CUDA(cudaMemcpyAsync(h->box.ints + 8, h->err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -207,7 +207,7 @@ template <class V, int K, bool XS_SCALED>
 __global__ void __launch_bounds__(kSellBlock)
     k_sell_prolong_jacobi_ap(SellView<V> AP, const V *__restrict__ dinv, const V *__restrict__ r,
                              const int *__restrict__ agg, const V *__restrict__ p, const V *__restrict__ xc,
-                             const V *__restrict__ xs, V *__restrict__ x) {
+                             const V *__restrict__ xs, V *__restrict__ x, double *__restrict__ x64) {
   pdl_begin();
   CWM_SELL_LANE(AP, K)
   V ri = V(0), di = V(0), yi = V(0);
@@ -217,22 +217,28 @@ __global__ void __launch_bounds__(kSellBlock)
     yi = fma(p[row], __ldg(xc + agg[row]), xs ? (XS_SCALED ? di * xs[row] : xs[row]) : V(0));
   }
   const V res = sell_row<V, K, false>(AP, base, L, j, xc, nullptr, ri);
-  if (in && j == 0) x[row] = fma(di, res, yi);
+  if (in && j == 0) {
+    const V xi = fma(di, res, yi);
+    x[row] = xi;
+    if (x64) x64[row] = (double)xi;
+  }
 }
 
 template <class V>
 amg_status sell_prolong_jacobi_ap(const SellView<V> &AP, int nc, const V *dinv, const V *r, const int *agg,
-                                  const V *p, const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s) {
+                                  const V *p, const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s,
+                                  double *x64) {
   if (AP.n == 0) return AMG_OK;
   CWM_TRACE("prolong_jacobi_sl", 16.0 * AP.n + (4.0 + sizeof(V)) * AP.nnz +
-                                     ((xs ? 5.0 : 4.0) * sizeof(V) + 4.0) * AP.n + sizeof(V) * (double)nc, s);
+                                     ((xs ? 5.0 : 4.0) * sizeof(V) + 4.0) * AP.n + sizeof(V) * (double)nc +
+                                     (x64 ? 8.0 * AP.n : 0.0), s);
   const int grid = grid_for((long long)sell_slices(AP.n, AP.lanes) * 32, kSellBlock, 1 << 30);
   if (xs_scaled)
     CWM_SELL_DISPATCH(AP.lanes, CWM_CUDA(launch_pdl(k_sell_prolong_jacobi_ap<V, kK, true>, grid, kSellBlock, 0, s,
-                                                    AP, dinv, r, agg, p, xc, xs, x)))
+                                                    AP, dinv, r, agg, p, xc, xs, x, x64)))
   else
     CWM_SELL_DISPATCH(AP.lanes, CWM_CUDA(launch_pdl(k_sell_prolong_jacobi_ap<V, kK, false>, grid, kSellBlock, 0, s,
-                                                    AP, dinv, r, agg, p, xc, xs, x)))
+                                                    AP, dinv, r, agg, p, xc, xs, x, x64)))
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -244,7 +250,7 @@ amg_status sell_prolong_jacobi_ap(const SellView<V> &AP, int nc, const V *dinv, 
   template amg_status sell_resid_restrict<V>(const SellView<V> &, int, const int *, const int *, const V *,         \
                                              const V *, const V *, const V *, V *, V *, cudaStream_t);             \
   template amg_status sell_prolong_jacobi_ap<V>(const SellView<V> &, int, const V *, const V *, const int *,       \
-                                                const V *, const V *, const V *, bool, V *, cudaStream_t);
+                                                const V *, const V *, const V *, bool, V *, cudaStream_t, double *);
 CWM_SELL_INST(double)
 CWM_SELL_INST(float)
 

@@ -15,12 +15,14 @@ constexpr int kBlock = 256;
 // full-mask shuffles are well defined; inactive tiles contribute zero.
 // NEG: returns init - sum_j a_ij x_j, lane 0 starting from init and every lane subtracting
 // its products (no separate FP64 subtraction).
-template <class V, int T, bool NEG = false>
+// SCALED: the vector entry is d_j x_j (x = D^{-1} b formed on the fly, d = D^{-1}).
+template <class V, int T, bool NEG = false, bool SCALED = false>
 __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int *__restrict__ ci,
                                           const V *__restrict__ val, const V *__restrict__ x, long long row,
-                                          bool active, int lane, V init = V(0)) {
+                                          bool active, int lane, V init = V(0), const V *__restrict__ d = nullptr) {
   V s = (NEG && lane == 0) ? init : V(0);
   const V sg = NEG ? V(-1) : V(1);
+  auto xj = [&](int j) { return SCALED ? __ldg(d + j) * __ldg(x + j) : __ldg(x + j); };
   if (active && x) {
     const int b = rp[row], e = rp[row + 1];
     int k = b + lane;
@@ -28,13 +30,13 @@ __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int 
     for (; k + 3 * T < e; k += 4 * T) {
       const int j0 = ci[k], j1 = ci[k + T], j2 = ci[k + 2 * T], j3 = ci[k + 3 * T];
       const V a0 = val[k], a1 = val[k + T], a2 = val[k + 2 * T], a3 = val[k + 3 * T];
-      const V x0 = __ldg(x + j0), x1 = __ldg(x + j1), x2 = __ldg(x + j2), x3 = __ldg(x + j3);
+      const V x0 = xj(j0), x1 = xj(j1), x2 = xj(j2), x3 = xj(j3);
       s = fma(sg * a0, x0, s);
       s = fma(sg * a1, x1, s);
       s = fma(sg * a2, x2, s);
       s = fma(sg * a3, x3, s);
     }
-    for (; k < e; k += T) s = fma(sg * val[k], __ldg(x + ci[k]), s);
+    for (; k < e; k += T) s = fma(sg * val[k], xj(ci[k]), s);
   }
 #pragma unroll
   for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
@@ -452,13 +454,24 @@ __global__ void __launch_bounds__(kRB) k_prolong_jacobi_rb(int n, const int *__r
   }
 }
 
+template <class V, int T, bool SCALED = false>
+__global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                     const V *__restrict__ val, const V *__restrict__ b,
+                                                     const V *__restrict__ x, V *__restrict__ r,
+                                                     const V *__restrict__ d = nullptr);
+
 template <class V>
 amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                                  const V *dinv, const V *b, V *r_scratch, V *bc, cudaStream_t s) {
   if (nc == 0) return AMG_OK;
   {
     CWM_TRACE("residual", 4.0 * (A.n + 1) + (4.0 + sizeof(V)) * A.nnz + 3.0 * sizeof(V) * A.n, s);
-    CWM_CUDA(launch_pdl(k_resid_scaled_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, r_scratch));
+    if (A.rb) {
+      CWM_CUDA(launch_pdl(k_resid_scaled_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, dinv, b, r_scratch));
+    } else {
+      CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_residual<V, kT, true>, rows_grid(A.n, kT), kBlock, 0, s, A.n,
+                                                 A.rp, A.ci, A.val, b, b, r_scratch, dinv)));
+    }
     CWM_LAUNCH();
   }
   return restrict_members<V>(A.n, nc, mptr, mlist, p, r_scratch, bc, s);
@@ -689,7 +702,7 @@ __global__ void __launch_bounds__(kRB) k_prolong_jacobi_ap_rb(int n, const int *
                                                               const V *__restrict__ dinv, const V *__restrict__ r,
                                                               const int *__restrict__ agg, const V *__restrict__ p,
                                                               const V *__restrict__ xc, const V *__restrict__ xs,
-                                                              V *__restrict__ x) {
+                                                              V *__restrict__ x, double *__restrict__ x64) {
   pdl_begin();
   __shared__ RowBlockSmem<V> sm;
   const int r0 = blockIdx.x * kRB;
@@ -705,7 +718,11 @@ __global__ void __launch_bounds__(kRB) k_prolong_jacobi_ap_rb(int n, const int *
     yi = fma(p[i], __ldg(xc + agg[i]), xs ? (XS_SCALED ? di * xs[i] : xs[i]) : V(0));
   }
   const V res = rb_row_dot<V, false, true>(ci, val, xc, nrows, sm, ri);
-  if (in) x[i] = fma(di, res, yi);
+  if (in) {
+    const V xi = fma(di, res, yi);
+    x[i] = xi;
+    if (x64) x64[i] = (double)xi;
+  }
 }
 
 template <class V, int T, bool XS_SCALED>
@@ -713,7 +730,7 @@ __global__ void __launch_bounds__(kBlock)
     k_prolong_jacobi_ap(int n, const int *__restrict__ rp, const int *__restrict__ ci, const V *__restrict__ val,
                         const V *__restrict__ dinv, const V *__restrict__ r, const int *__restrict__ agg,
                         const V *__restrict__ p, const V *__restrict__ xc, const V *__restrict__ xs,
-                        V *__restrict__ x) {
+                        V *__restrict__ x, double *__restrict__ x64) {
   pdl_begin();
   CWM_TILE_LOOP(T, n) {
     const long long row = base + sub;
@@ -725,31 +742,36 @@ __global__ void __launch_bounds__(kBlock)
       yi = fma(p[row], __ldg(xc + agg[row]), xs ? (XS_SCALED ? di * xs[row] : xs[row]) : V(0));
     }
     const V res = tile_row_dot<V, T, true>(rp, ci, val, xc, row, active, lane, ri);
-    if (active && lane == 0) x[row] = fma(di, res, yi);
+    if (active && lane == 0) {
+      const V xi = fma(di, res, yi);
+      x[row] = xi;
+      if (x64) x64[row] = (double)xi;
+    }
   }
 }
 
 template <class V, bool XS_SCALED>
 static amg_status launch_prolong_jacobi_ap(const CsrView<V> &AP, const V *dinv, const V *r, const int *agg,
-                                           const V *p, const V *xc, const V *xs, V *x, cudaStream_t s) {
+                                           const V *p, const V *xc, const V *xs, V *x, double *x64, cudaStream_t s) {
   if (AP.rb) {
     CWM_CUDA(launch_pdl(k_prolong_jacobi_ap_rb<V, XS_SCALED>, rb_grid(AP.n), kRB, 0, s, AP.n, AP.rp, AP.ci, AP.val,
-                        dinv, r, agg, p, xc, xs, x));
+                        dinv, r, agg, p, xc, xs, x, x64));
   } else {
     CWM_DISPATCH_T(AP.tile, CWM_CUDA(launch_pdl(k_prolong_jacobi_ap<V, kT, XS_SCALED>, rows_grid(AP.n, kT), kBlock, 0,
-                                                s, AP.n, AP.rp, AP.ci, AP.val, dinv, r, agg, p, xc, xs, x)));
+                                                s, AP.n, AP.rp, AP.ci, AP.val, dinv, r, agg, p, xc, xs, x, x64)));
   }
   return AMG_OK;
 }
 
 template <class V>
 amg_status prolong_jacobi_ap(const CsrView<V> &AP, int nc, const V *dinv, const V *r, const int *agg, const V *p,
-                             const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s) {
+                             const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s, double *x64) {
   if (AP.n == 0) return AMG_OK;
-  CWM_TRACE("prolong_jacobi", 4.0 * (AP.n + 1) + (4.0 + sizeof(V)) * AP.nnz +
-                                  ((xs ? 5.0 : 4.0) * sizeof(V) + 4.0) * AP.n + sizeof(V) * (double)nc, s);
-  if (xs_scaled) CWM_TRY((launch_prolong_jacobi_ap<V, true>(AP, dinv, r, agg, p, xc, xs, x, s)));
-  else CWM_TRY((launch_prolong_jacobi_ap<V, false>(AP, dinv, r, agg, p, xc, xs, x, s)));
+  CWM_TRACE("prolong_jacobi_ap", 4.0 * (AP.n + 1) + (4.0 + sizeof(V)) * AP.nnz +
+                                     ((xs ? 5.0 : 4.0) * sizeof(V) + 4.0) * AP.n + sizeof(V) * (double)nc +
+                                  (x64 ? 8.0 * AP.n : 0.0), s);
+  if (xs_scaled) CWM_TRY((launch_prolong_jacobi_ap<V, true>(AP, dinv, r, agg, p, xc, xs, x, x64, s)));
+  else CWM_TRY((launch_prolong_jacobi_ap<V, false>(AP, dinv, r, agg, p, xc, xs, x, x64, s)));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -770,16 +792,19 @@ __global__ void __launch_bounds__(kRB) k_resid_rb(int n, const int *__restrict__
   if (threadIdx.x < nrows) r[i] = res;
 }
 
-// r = b - A x (x may be NULL: r = b), a sub-warp tile per row
-template <class V, int T>
+// r = b - A x (x may be NULL: r = b), a sub-warp tile per row; SCALED: r = b - A (D^{-1} b)
+// with x = b and d = D^{-1}
+template <class V, int T, bool SCALED>
 __global__ void __launch_bounds__(kBlock) k_residual(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                      const V *__restrict__ val, const V *__restrict__ b,
-                                                     const V *__restrict__ x, V *__restrict__ r) {
+                                                     const V *__restrict__ x, V *__restrict__ r,
+                                                     const V *__restrict__ d) {
   pdl_begin();
   CWM_TILE_LOOP(T, n) {
     const long long row = base + sub;
     const bool active = row < n;
-    const V res = tile_row_dot<V, T, true>(rp, ci, val, x, row, active, lane, active && lane == 0 ? b[row] : V(0));
+    const V res = tile_row_dot<V, T, true, SCALED>(rp, ci, val, x, row, active, lane,
+                                                   active && lane == 0 ? b[row] : V(0), d);
     if (active && lane == 0) r[row] = x ? res : b[row];
   }
 }
@@ -789,8 +814,8 @@ static amg_status launch_residual(const CsrView<V> &A, const V *b, const V *x, V
   if (A.rb) {
     CWM_CUDA(launch_pdl(k_resid_rb<V>, rb_grid(A.n), kRB, 0, s, A.n, A.rp, A.ci, A.val, b, x, r));
   } else {
-    CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_residual<V, kT>, rows_grid(A.n, kT), kBlock, 0, s, A.n, A.rp, A.ci, A.val, b, x,
-                                                                                  r)));
+    CWM_DISPATCH_T(A.tile, CWM_CUDA(launch_pdl(k_residual<V, kT>, rows_grid(A.n, kT), kBlock, 0, s, A.n, A.rp, A.ci,
+                                               A.val, b, x, r, (const V *)nullptr)));
   }
   return AMG_OK;
 }
@@ -1181,7 +1206,7 @@ amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const do
 // d = w - coef d, x += step d;  q = v - coef q, r -= step q;  then partial r.r.
 __global__ void __launch_bounds__(kBlock)
     k_fcg_update(int n, const double *__restrict__ w, const double *__restrict__ v, double *__restrict__ d,
-                 double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
+                 double *__restrict__ q, double *__restrict__ x, double *__restrict__ r, float *__restrict__ r32,
                  double *__restrict__ scal, double *__restrict__ part, unsigned *tick, int first, int vec) {
   pdl_begin();
   const bool broken = scal[kFlags] != 0.0;  // breakdown: leave x, r, d, q as they were
@@ -1213,6 +1238,7 @@ __global__ void __launch_bounds__(kBlock)
         *reinterpret_cast<double2 *>(x + i) = make_double2(fma(step, d2.x, x2.x), fma(step, d2.y, x2.y));
         const double2 rn = make_double2(fma(-step, q2.x, r2.x), fma(-step, q2.y, r2.y));
         *reinterpret_cast<double2 *>(r + i) = rn;
+        if (r32) *reinterpret_cast<float2 *>(r32 + i) = make_float2((float)rn.x, (float)rn.y);
         rr = fma(rn.x, rn.x, rr);
         rr = fma(rn.y, rn.y, rr);
       } else {
@@ -1224,6 +1250,7 @@ __global__ void __launch_bounds__(kBlock)
           x[j] = fma(step, dj, x[j]);
           const double rj = fma(-step, qj, r[j]);
           r[j] = rj;
+          if (r32) r32[j] = (float)rj;
           rr = fma(rj, rj, rr);
         }
       }
@@ -1248,11 +1275,12 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 amg_status fcg_update(int n, const double *w, const double *v, double *d, double *q, double *x, double *r,
-                      double *scal, double *part, unsigned *tick, int first, cudaStream_t s) {
-  CWM_TRACE("fcg_update", (first ? 64.0 : 80.0) * n, s);
+                      float *r32, double *scal, double *part, unsigned *tick, int first, cudaStream_t s) {
+  CWM_TRACE("fcg_update", (first ? 64.0 : 80.0) * n + (r32 ? 4.0 * n : 0.0), s);
   auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-  const int vec = al(w) && al(v) && al(d) && al(q) && al(x) && al(r);
-  CWM_CUDA(launch_pdl(k_fcg_update, fcg_update_blocks(n), kRB, 0, s, n, w, v, d, q, x, r, scal, part, tick, first, vec));
+  const int vec = al(w) && al(v) && al(d) && al(q) && al(x) && al(r) && (((uintptr_t)r32 & 7u) == 0);
+  CWM_CUDA(launch_pdl(k_fcg_update, fcg_update_blocks(n), kRB, 0, s, n, w, v, d, q, x, r, r32, scal, part, tick, first,
+                      vec));
   CWM_LAUNCH();
   return AMG_OK;
 }
@@ -1323,7 +1351,7 @@ amg_status to_double(long long n, const float *x, double *y, cudaStream_t s) {
   template amg_status prolong_jacobi<V>(const CsrView<V> &, const V *, const V *, const int *, const V *,    \
                                         const V *, V *, cudaStream_t);                                       \
   template amg_status prolong_jacobi_ap<V>(const CsrView<V> &, int, const V *, const V *, const int *, const V *, \
-                                           const V *, const V *, bool, V *, cudaStream_t);                    \
+                                           const V *, const V *, bool, V *, cudaStream_t, double *);          \
   template amg_status add_to<V>(int, const V *, V *, cudaStream_t);                                          \
   template amg_status restrict_members<V>(int, int, const int *, const int *, const V *, const V *, V *,      \
                                           cudaStream_t);

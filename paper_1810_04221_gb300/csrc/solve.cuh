@@ -65,7 +65,8 @@ amg_status dense_coarse_apply(int n, const V *X, const V *b, V *y, cudaStream_t 
 template <class V>
 amg_status resid_restrict_rb(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                              const V *b, const V *x, V *r_scratch, V *bc, cudaStream_t s);
-// r = b - A (D^{-1} b) into r_scratch, then bc = P^T r (the first sweep from zero fused in)
+// r = b - A (D^{-1} b) into r_scratch, then bc = P^T r (the first sweep from zero fused in;
+// row blocks or sub-warp tiles as A's shape says)
 template <class V>
 amg_status resid_scaled_restrict(const CsrView<V> &A, int nc, const int *mptr, const int *mlist, const V *p,
                                  const V *dinv, const V *b, V *r_scratch, V *bc, cudaStream_t s);
@@ -83,10 +84,11 @@ amg_status ap_group(int n, long long nnz, const int *rp, const int *ci, const do
                     cudaStream_t s);
 // x = y + D^{-1} (r - (A P) xc) with y = xs + P xc and r = b - A xs: the coarse correction
 // and one post-sweep (xs may be NULL: 0; xs_scaled: xs holds b and the pre-sweep result is
-// D^{-1} b); AP: the stored product A P, nc: columns of P
+// D^{-1} b); AP: the stored product A P, nc: columns of P; x64 != NULL: x also written in
+// binary64 there
 template <class V>
 amg_status prolong_jacobi_ap(const CsrView<V> &AP, int nc, const V *dinv, const V *r, const int *agg, const V *p,
-                             const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s);
+                             const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s, double *x64 = nullptr);
 // r = b - A x (any value type)
 template <class V>
 amg_status residual_t(const CsrView<V> &A, const V *b, const V *x, V *r, cudaStream_t s);
@@ -206,7 +208,8 @@ amg_status sell_resid_restrict(const SellView<V> &A, int nc, const int *mptr, co
 // prolong_jacobi_ap on the sliced A P
 template <class V>
 amg_status sell_prolong_jacobi_ap(const SellView<V> &AP, int nc, const V *dinv, const V *r, const int *agg,
-                                  const V *p, const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s);
+                                  const V *p, const V *xc, const V *xs, bool xs_scaled, V *x, cudaStream_t s,
+                                  double *x64 = nullptr);
 
 // spmv_dots_scalars on the 3x3-block layout (part holds 3 * part_blocks doubles)
 amg_status block3_spmv_dots(const Sell3View<double> &A, const double *w, const double *r, const double *q, double *v,
@@ -224,7 +227,9 @@ int fcg_update_blocks(int n);    // partial sums written by fcg_update
 amg_status spmv_dots_scalars(const CsrView<double> &A, const double *w, const double *r, const double *q,
                              double *v, double *part, double *scal, unsigned *tick, int first, cudaStream_t s);
 // d = w - coef d; q = v - coef q; x += step d; r -= step q; r.r into scal[kRR] (last block)
+// (r32 != NULL: also r32 = the new r rounded to binary32, the next float32 V-cycle's input)
 amg_status fcg_update(int n, const double *w, const double *v, double *d, double *q, double *x, double *r,
+                      float *r32,
                       double *scal, double *part, unsigned *tick, int first, cudaStream_t s);
 // scal[slot] = sum of part[0..nb)
 amg_status reduce_into(int nb, const double *part, double *scal, int slot, cudaStream_t s);

@@ -148,9 +148,8 @@ def test_vcycle_coupled_post(case, coupled, fp32):
         h.free()
     ref = H.vcycle(r)
     assert np.abs(got - ref).max() <= (FP32_TOL if fp32 else 1e-12) * np.abs(ref).max()
-    # level 0 through A P: no separate post-sweep `jacobi`, and a pre-sweep `scale` or (on
-    # the 3x3-block layout of elasticity) the pre-sweep formed inside the residual
-    used = ("scale@0" in names or "residual_b3@0" in names) and "jacobi@0" not in names
+    # level 0 through A P (stored in CSR or sliced), and no separate post-sweep `jacobi`
+    used = ("prolong_jacobi_ap@0" in names or "prolong_jacobi_sl@0" in names) and "jacobi@0" not in names
     if name.startswith("poisson3d"):  # 7-entry rows: auto mode leaves them to the separate passes
         assert used == (coupled == 1)
     if name.startswith("elasticity"):  # 81-entry rows on sub-warp tiles: auto builds A P
