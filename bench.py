@@ -339,6 +339,15 @@ def run_cuda(args, rank, world, dist):
                     "traffic": _traffic_for(dominant), "launches": nl,
                     "bytes_per_launch": byt / nl, "avg_launch_us": ms / nl * 1e3}
             roof["classes"] = class_rooflines(trace_all, peak)
+            # the FP64-issue-bound classes against the FP64 rates measured on this GPU now
+            try:
+                r_fma, r_div = B.cwm_fp64_rates()
+                roof["fp64"] = {"probe": "cwm_fp64_rates: 8 independent FP64 chains per thread, 8 blocks of 256 "
+                                         "threads per SM, CUDA events", "fma_per_s": r_fma, "div_per_s": r_div,
+                                "classes": fp64_fractions(roof["classes"], n, nnz, int(np.count_nonzero(val)),
+                                                          r_fma, r_div)}
+            except Exception as exc:  # noqa: BLE001
+                roof["fp64"] = {"error": str(exc)}
 
     # precision variants on the same workload (not part of the timed value): the other
     # V-cycle precision, and binary32 Galerkin products for every coarse operator with the
@@ -429,6 +438,27 @@ def class_rooflines(trace, peak):
         out.append({"kernel": e["name"], "launches": e["launches"], "total_ms": round(e["total_ms"], 4),
                     "bytes_per_launch": round(bpl), "avg_launch_us": round(us, 2),
                     "achieved_gbs": round(bpl / us * 1e-3, 1), "frac": round(bpl / us * 1e-3 / peak, 4)})
+    return out
+
+
+def fp64_fractions(classes, n, nnz, nnz_nonzero, r_fma, r_div):
+    """FP64 issue fraction of the FP64-bound classes: the time their FP64 operations take at
+    the measured rates over their measured launch time.  spmv_dots: one FMA per stored entry
+    and three per row (the dot products); weights@0 (the first sweep on the input operator):
+    per stored off-diagonal nonzero pair three multiplies, two adds and one division."""
+    out = []
+    edges = max(nnz_nonzero - n, 0) / 2.0
+    for c in classes:
+        if c["kernel"] in ("spmv_dots", "spmv_dots_b3"):
+            t = (nnz + 3.0 * n) / r_fma
+            what = "(nnz + 3n) FMA"
+        elif c["kernel"] == "weights@0":
+            t = edges * (5.0 / r_fma + 1.0 / r_div)
+            what = "per edge 5 FP64 ops + 1 division"
+        else:
+            continue
+        out.append({"kernel": c["kernel"], "ops": what, "fp64_us": round(t * 1e6, 2),
+                    "avg_launch_us": c["avg_launch_us"], "fp64_frac": round(t * 1e6 / c["avg_launch_us"], 4)})
     return out
 
 

@@ -280,6 +280,14 @@ amg_status amg_trace_get(amg_handle h, int i, amg_trace_entry *out);
 /* Kernel launches made by this library in this process so far (all handles, all calls). */
 int64_t amg_launch_count(void);
 
+/* Measured FP64 issue rates of the current device (the paper has no counterpart: these are
+ * the denominators against which the FP64-bound kernels are reported).  *fma_per_s: fused
+ * multiply-adds per second, all SMs, independent chains; *div_per_s: correctly rounded
+ * divisions per second, measured the same way.  Host pointers.  Ordered on `stream`; takes
+ * a few milliseconds and allocates 8 bytes of device memory.  Errors: INVALID_ARG (NULL
+ * output), CUDA.  Synchronises. */
+amg_status cwm_fp64_rates(double *fma_per_s, double *div_per_s, void *stream);
+
 /* Human-readable name of a status, and the last error message of the calling thread. */
 const char *amg_status_string(amg_status s);
 const char *amg_last_error(void);

@@ -25,7 +25,7 @@ EXPORTS = (
     "amg_num_levels", "amg_level_info", "amg_level_export", "amg_sweep_mate", "cwm_edge_weights",
     "cwm_suitor_match", "cwm_aggregate", "cwm_galerkin", "amg_status_string", "amg_last_error",
     "amg_trace_enable", "amg_trace_reset", "amg_trace_count", "amg_trace_get", "amg_launch_count",
-    "cwm_suitor_match_noalloc", "cwm_pattern_outer",
+    "cwm_suitor_match_noalloc", "cwm_pattern_outer", "cwm_fp64_rates",
 )
 
 
@@ -117,6 +117,7 @@ def load(path: str | None = None):
             "amg_trace_count": (i, [vp]),
             "amg_trace_get": (i, [vp, i, C.POINTER(AmgTraceEntry)]),
             "amg_launch_count": (i64, []),
+            "cwm_fp64_rates": (i, [C.POINTER(d), C.POINTER(d), vp]),
             "amg_status_string": (C.c_char_p, [i]),
             "amg_last_error": (C.c_char_p, []),
         }
@@ -360,3 +361,10 @@ def cwm_pattern_outer(row_ptr, col, lam, x, alpha: float = 1.0, out=None, stream
                                     _dev(lam, torch.float64, "lam", n), _dev(x, torch.float64, "x", n), float(alpha),
                                     _dev(out, torch.float64, "out", nnz), _stream(stream)), "cwm_pattern_outer")
     return out
+
+
+def cwm_fp64_rates(stream=None) -> tuple[float, float]:
+    """(fused multiply-adds per second, correctly rounded divisions per second) in FP64."""
+    f, d = C.c_double(), C.c_double()
+    _check(load().cwm_fp64_rates(C.byref(f), C.byref(d), _stream(stream)), "cwm_fp64_rates")
+    return f.value, d.value

@@ -223,6 +223,14 @@ struct LevelTag {
   ~LevelTag() { g_trace_level = prev; }
 };
 
+// Tags the setup classes of a level's later matching sweeps (s >= 1) as @k.s, so that the
+// @k classes time the first sweep, the one on the level operator itself.
+struct SweepTag {
+  int prev;
+  explicit SweepTag(int s) : prev(g_trace_sweep) { g_trace_sweep = s; }
+  ~SweepTag() { g_trace_sweep = prev; }
+};
+
 amg_status read_err(amg_hierarchy *h, const char *where) {
   CWM_CUDA(cudaMemcpyAsync(h->box.ints + 8, h->err.get(), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CWM_CUDA(cudaStreamSynchronize(h->stream));
@@ -292,6 +300,7 @@ amg_status coarsen_level(amg_hierarchy *h, bool *made) {
   F.sweep_mate.clear();
 
   for (int sweep = 0; sweep < S; ++sweep) {
+    SweepTag stag(sweep);
     // every operator after the input is symmetric by construction (P^T A P of a symmetric
     // A), so only the input's weights need the cleared array
     CWM_TRY(edge_weights(cn, cnnz, crp, cci, cval, cdiag, cv, w.get(), dv.get(), s,

@@ -48,11 +48,14 @@ void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_rel
 
 thread_local Tracer *g_tracer = nullptr;
 thread_local int g_trace_level = -1;
+thread_local int g_trace_sweep = 0;
 
 TraceScope::TraceScope(const char *cat, double b, cudaStream_t st) : s(st), bytes(b) {
   if (!g_tracer || !g_tracer->on) return;
   char name[64];
-  if (g_trace_level >= 0) snprintf(name, sizeof(name), "%s@%d", cat, g_trace_level);
+  if (g_trace_level >= 0 && g_trace_sweep > 0)
+    snprintf(name, sizeof(name), "%s@%d.%d", cat, g_trace_level, g_trace_sweep);
+  else if (g_trace_level >= 0) snprintf(name, sizeof(name), "%s@%d", cat, g_trace_level);
   else snprintf(name, sizeof(name), "%s", cat);
   if (!g_tracer->wants(name)) return;
   t = g_tracer;

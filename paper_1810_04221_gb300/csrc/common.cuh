@@ -108,6 +108,7 @@ void count_launches(long long k);
 struct Tracer;
 extern thread_local Tracer *g_tracer;
 extern thread_local int g_trace_level;  // appended to category names as @k when >= 0
+extern thread_local int g_trace_sweep;  // s >= 1: the (s+1)-th matching sweep of a level, @k.s
 struct TraceScope {
   Tracer *t = nullptr;
   int idx = -1;

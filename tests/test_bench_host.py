@@ -108,3 +108,13 @@ def test_class_rooflines():
     out = bench.class_rooflines(tr, 5000.0)
     assert len(out) == 1 and out[0]["avg_launch_us"] == 100.0
     assert out[0]["achieved_gbs"] == 5000.0 and out[0]["frac"] == 1.0
+
+
+def test_fp64_fractions():
+    cls = [{"kernel": "spmv_dots_b3", "avg_launch_us": 100.0}, {"kernel": "weights@0", "avg_launch_us": 50.0},
+           {"kernel": "residual@0", "avg_launch_us": 10.0}]
+    out = bench.fp64_fractions(cls, n=1000, nnz=10000, nnz_nonzero=9000, r_fma=1e9, r_div=1e8)
+    assert [o["kernel"] for o in out] == ["spmv_dots_b3", "weights@0"]
+    assert abs(out[0]["fp64_us"] - 13.0) < 1e-9 and abs(out[0]["fp64_frac"] - 0.13) < 1e-9
+    # 4000 edges x (5 / 1e9 + 1 / 1e8) s = 60 us
+    assert abs(out[1]["fp64_us"] - 60.0) < 1e-9 and abs(out[1]["fp64_frac"] - 1.2) < 1e-9
