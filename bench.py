@@ -66,7 +66,7 @@ def workload(name: str):
         sweeps, cmax, fp32 = 3, 1000, True
         desc = (f"3D FV diffusion {m}^3, log-kappa N(0,4), 3 sweeps/level, coarse<=1000, stall ratio 1.2, "
                 "FP32 V-cycle in FP64 FCG")
-    elif name in ("elasticity_64", "elasticity_32"):
+    elif name in ("elasticity_64", "elasticity_48", "elasticity_32"):
         m = int(name.split("_")[1])
         mat = P.elasticity_q1(m)
         n = len(mat[0]) - 1
@@ -88,8 +88,10 @@ def workload(name: str):
 # the ratio of stored entries.  The full-size iteration count is higher than the sample's,
 # so the scaled figure underestimates the oracle's full-size time.
 CPU_SAMPLE = {"poisson3d_128": "poisson3d_128", "poisson2d_64": "poisson2d_64",
-              "lognormal_160": "lognormal_80", "elasticity_64": "elasticity_32"}
-WORKLOADS = ["elasticity_64", "poisson3d_128", "lognormal_160", "poisson2d_64"]
+              "lognormal_160": "lognormal_80", "elasticity_64": "elasticity_32", "elasticity_48": "elasticity_32"}
+# elasticity_48 (n = 324,864, 25.2M entries, the 3x3-block copy 213 MB > L2) is the
+# profiling-size case of the elasticity family
+WORKLOADS = ["elasticity_64", "poisson3d_128", "lognormal_160", "poisson2d_64", "elasticity_48"]
 
 
 def bench_config(name: str, n: int, nnz: int, desc: str, sweeps: int, cmax: int, rtol: float, fp32: bool,
@@ -435,9 +437,13 @@ def class_rooflines(trace, peak):
             continue
         us = e["total_ms"] / e["launches"] * 1e3
         bpl = e["bytes"] / e["launches"]
-        out.append({"kernel": e["name"], "launches": e["launches"], "total_ms": round(e["total_ms"], 4),
-                    "bytes_per_launch": round(bpl), "avg_launch_us": round(us, 2),
-                    "achieved_gbs": round(bpl / us * 1e-3, 1), "frac": round(bpl / us * 1e-3 / peak, 4)})
+        row = {"kernel": e["name"], "launches": e["launches"], "total_ms": round(e["total_ms"], 4),
+               "bytes_per_launch": round(bpl), "avg_launch_us": round(us, 2),
+               "achieved_gbs": round(bpl / us * 1e-3, 1), "frac": round(bpl / us * 1e-3 / peak, 4)}
+        tr = _traffic_for(e["name"])
+        if tr is not None:
+            row["traffic"] = tr
+        out.append(row)
     return out
 
 
