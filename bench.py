@@ -325,6 +325,15 @@ def run_cuda(args, rank, world, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
+    # the host -> device copies of one step alone (what e2e adds to the device-resident step)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    g_copy = [t.cuda(non_blocking=True) for t in (h_rp, h_ci, h_val, h_v, h_b)]
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_ms = c0.elapsed_time(c1)
+    del g_copy
 
     # roofline of the dominant kernel class over the timed region
     peak, peak_kind = _peaks()
@@ -417,7 +426,8 @@ def run_cuda(args, rank, world, dist):
         "rel_res_true": last["rel_res_true"], "err_vs_xstar": err, "err_vs_oracle": err_oracle,
         "oracle_iters": oracle_iters, "input_check": check_cost,
         "status": [B.status_name(s) for s in statuses][-1],
-        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "h2d_ms": round(h2d_ms, 3), "h2d_gbs": round(h2d / (h2d_ms * 1e-3) / 1e9, 1)},
         "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "kernel_classes": sorted([{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
                                   for e in trace_all], key=lambda e: -e["total_ms"])[:12],

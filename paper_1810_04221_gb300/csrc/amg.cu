@@ -1014,23 +1014,44 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
     if (P.stall_ratio > 0.0 && (double)Fl.n < P.stall_ratio * (double)Cl.n) break;
   }
   for (Level &L : h->lev) CWM_TRY(finish_level(h, L));
-  CWM_TRY(build_block3(h));
   h->lev.back().nsweeps = 0;
+  CWM_CUDA(cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking));
+  CWM_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CWM_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  // The coarsest level's dense operator (FP64-bound) is built on the library's second stream
+  // while the setup stream builds the 3x3-block copy, A P and the sliced copies (latency-bound
+  // kernels); the setup stream waits for it before anything else is released or returned,
+  // on every path out of this function (Join runs before dense_tmp is freed).
+  DBuf<double> dense_tmp;
+  struct Join {
+    cudaStream_t side = nullptr, main = nullptr;
+    cudaEvent_t ev = nullptr;
+    ~Join() {
+      if (!side) return;
+      cudaEventRecord(ev, side);
+      cudaStreamWaitEvent(main, ev, 0);
+    }
+  } join;
   {
     Level &Lc = h->lev.back();
     LevelTag tag((int)h->lev.size() - 1);
     if (Lc.n <= kDenseCoarseMax) {
       const size_t nn = (size_t)Lc.n * Lc.n;
-      DBuf<double> tmp;
       CWM_TRY(Lc.xdense.alloc(nn, s));
-      CWM_TRY(tmp.alloc(nn, s));
-      CWM_TRY(dense_coarse_build(Lc.view64(), Lc.dinv.get(), P.coarse_sweeps, Lc.xdense.get(), tmp.get(), s));
-      if (P.vcycle_fp32) {
-        CWM_TRY(Lc.xdense32.alloc(nn, s));
-        CWM_TRY(to_float((long long)nn, Lc.xdense.get(), Lc.xdense32.get(), s));
-      }
+      CWM_TRY(dense_tmp.alloc(nn, s));
+      if (P.vcycle_fp32) CWM_TRY(Lc.xdense32.alloc(nn, s));
+      cudaStream_t side = h->solve_stream;
+      CWM_CUDA(cudaEventRecord(h->ev_in, s));
+      CWM_CUDA(cudaStreamWaitEvent(side, h->ev_in, 0));
+      join.side = side;
+      join.main = s;
+      join.ev = h->ev_out;
+      CWM_TRY(dense_coarse_build(Lc.view64(), Lc.dinv.get(), P.coarse_sweeps, Lc.xdense.get(), dense_tmp.get(),
+                                 side));
+      if (P.vcycle_fp32) CWM_TRY(to_float((long long)nn, Lc.xdense.get(), Lc.xdense32.get(), side));
     }
   }
+  CWM_TRY(build_block3(h));
 
   // the fused coarse end of the V-cycle
   {
@@ -1067,9 +1088,11 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   CWM_TRY(h->scal.alloc(kFcgSlots, s));
   CWM_TRY(h->tick.alloc(4, s));
   CWM_CUDA(cudaMemsetAsync(h->tick.get(), 0, 4 * sizeof(unsigned), s));
-  CWM_CUDA(cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking));
-  CWM_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
-  CWM_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  if (join.side) {  // join the dense build before the final synchronisation
+    CWM_CUDA(cudaEventRecord(h->ev_out, join.side));
+    CWM_CUDA(cudaStreamWaitEvent(s, h->ev_out, 0));
+    join.side = nullptr;
+  }
   CWM_CUDA(cudaStreamSynchronize(s));
   return AMG_OK;
 }
