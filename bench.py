@@ -315,16 +315,21 @@ def run_cuda(args, rank, world, dist):
         torch.cuda.current_stream().synchronize()
         hh.free()
 
-    e2e_step()
+    for _ in range(2):
+        e2e_step()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
+        es[k].record(stream)
         e2e_step()
+    es[args.steps].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_steps = [round(es[k].elapsed_time(es[k + 1]), 3) for k in range(args.steps)]
     # the host -> device copies of one step alone (what e2e adds to the device-resident step)
     c0 = torch.cuda.Event(enable_timing=True)
     c1 = torch.cuda.Event(enable_timing=True)
@@ -427,7 +432,8 @@ def run_cuda(args, rank, world, dist):
         "oracle_iters": oracle_iters, "input_check": check_cost,
         "status": [B.status_name(s) for s in statuses][-1],
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "h2d_ms": round(h2d_ms, 3), "h2d_gbs": round(h2d / (h2d_ms * 1e-3) / 1e9, 1)},
+                "h2d_ms": round(h2d_ms, 3), "h2d_gbs": round(h2d / (h2d_ms * 1e-3) / 1e9, 1),
+                "median_ms": round(statistics.median(e2e_steps), 3), "steps_ms": e2e_steps},
         "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "kernel_classes": sorted([{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
                                   for e in trace_all], key=lambda e: -e["total_ms"])[:12],
