@@ -26,6 +26,9 @@ constexpr int kWarpCap = 256;     // keys per warp (sorted in registers, kept in
 constexpr int kWarpsPerBlock = 8;
 constexpr int kBlockCap = 8192;   // keys per long row (64 KB of dynamic shared memory)
 constexpr int kLongThreads = 256;
+#ifndef CWM_GALERKIN_KEY32
+#define CWM_GALERKIN_KEY32 1
+#endif
 
 struct RowSrc {
   int i1, i2;  // members (i2 < 0: singleton)
@@ -238,8 +241,8 @@ __device__ __forceinline__ void galerkin_row_reg(const RowSrc &r, int I, unsigne
 // Bitonic sort of the warp's 32 * E keys held in registers, key q = lane * E + e: stages
 // with j < E compare within a lane, the others exchange with lane ^ (j / E) by shuffles.
 // All loops unroll, so the array stays in registers.
-template <int E>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&a)[E], int lane) {
+template <int E, class K>
+__device__ __forceinline__ void warp_bitonic(K (&a)[E], int lane) {
 #pragma unroll
   for (int k = 2; k <= 32 * E; k <<= 1) {
 #pragma unroll
@@ -250,7 +253,7 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&a)[E], int lan
           const int f = e ^ j;
           if (f > e) {
             const bool up = ((lane * E + e) & k) == 0;
-            const unsigned long long x = a[e], y = a[f];
+            const K x = a[e], y = a[f];
             if ((x > y) == up) { a[e] = y; a[f] = x; }
           }
         }
@@ -259,7 +262,7 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&a)[E], int lan
         const bool lower = (lane & lm) == 0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const unsigned long long o = __shfl_xor_sync(0xffffffffu, a[e], lm);
+          const K o = __shfl_xor_sync(0xffffffffu, a[e], lm);
           const bool up = ((lane * E + e) & k) == 0;
           a[e] = (lower == up) ? (a[e] < o ? a[e] : o) : (a[e] < o ? o : a[e]);
         }
@@ -268,19 +271,35 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&a)[E], int lan
   }
 }
 
-// Keys (J, slot) of a coarse row with L <= 32 * E entries, sorted into keys[0 .. 32E).
-template <int E>
+// Keys (J, slot) of a coarse row with L <= 32 * E entries, sorted into keys[0 .. 32E) as
+// (J << 32) | slot.  K32 (every J below 2^24 - 1): the register sort runs on 32-bit keys
+// (J << 8) | slot -- slots are below 256 -- half the shuffles and compares of 64-bit keys.
+template <int E, bool K32>
 __device__ __forceinline__ void sort_row_keys(const RowSrc &r, int L, unsigned long long *keys,
                                               const int *__restrict__ ci, const int *__restrict__ agg, int lane) {
-  unsigned long long a[E];
+  if (K32) {
+    unsigned a[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int q = lane * E + e;
-    a[e] = q < L ? make_key(r, q, ci, agg) : ~0ull;
+    for (int e = 0; e < E; ++e) {
+      const int q = lane * E + e;
+      const unsigned long long k = q < L ? make_key(r, q, ci, agg) : 0ull;
+      a[e] = q < L ? (unsigned)((k >> 32) << 8) | (unsigned)(k & 0xffu) : ~0u;
+    }
+    warp_bitonic<E>(a, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      keys[lane * E + e] = ((unsigned long long)(a[e] >> 8) << 32) | (unsigned long long)(a[e] & 0xffu);
+  } else {
+    unsigned long long a[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int q = lane * E + e;
+      a[e] = q < L ? make_key(r, q, ci, agg) : ~0ull;
+    }
+    warp_bitonic<E>(a, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) keys[lane * E + e] = a[e];
   }
-  warp_bitonic<E>(a, lane);
-#pragma unroll
-  for (int e = 0; e < E; ++e) keys[lane * E + e] = a[e];
   __syncwarp();
 }
 
@@ -291,7 +310,7 @@ __device__ __forceinline__ void sort_row_keys(const RowSrc &r, int L, unsigned l
 // first position of each run of equal J: orders the run's (at most four) terms by their
 // canonical keys and sums them.  The FP64 products then run on full warps; only the few
 // additions of each run run on its first lane.
-template <class Acc>
+template <class Acc, bool K32>
 __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsigned long long *keys, double *tq,
                                                   unsigned *jq, const int *__restrict__ ci,
                                                   const double *__restrict__ val, const int *__restrict__ agg,
@@ -300,9 +319,9 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
                                                   double *__restrict__ valc, double *__restrict__ diag_c, int *err) {
   const int lane = threadIdx.x & 31;
   const int L = r.L1 + r.L2;
-  if (L <= 64) sort_row_keys<2>(r, L, keys, ci, agg, lane);
-  else if (L <= 128) sort_row_keys<4>(r, L, keys, ci, agg, lane);
-  else sort_row_keys<8>(r, L, keys, ci, agg, lane);
+  if (L <= 64) sort_row_keys<2, K32>(r, L, keys, ci, agg, lane);
+  else if (L <= 128) sort_row_keys<4, K32>(r, L, keys, ci, agg, lane);
+  else sort_row_keys<8, K32>(r, L, keys, ci, agg, lane);
   for (int q = lane; q < L; q += 32) {
     const unsigned long long key = keys[q];
     const int local = (int)(key & 0xffffffffu);
@@ -369,7 +388,7 @@ __device__ __forceinline__ void galerkin_row_smem(const RowSrc &r, int I, unsign
 // kernel).
 // Columns and values of row I at rpc[I] (the padded offsets), and cnt[I] = its number of
 // distinct J.
-template <class Acc>
+template <class Acc, bool K32>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_galerkin_warp(int nc, const int *__restrict__ rp, const int *__restrict__ ci,
                     const double *__restrict__ val, const int *__restrict__ m1,
@@ -411,7 +430,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       if (L <= 32) {
         galerkin_row_reg<Acc>(r, I, 0xffffffffu, 0, 32, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (L <= kWarpCap) {
-        galerkin_row_smem<Acc>(r, I, keys, tq, jq, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
+        galerkin_row_smem<Acc, K32>(r, I, keys, tq, jq, ci, val, agg, p, cnt, rpc, cic, valc, diag_c, err);
       } else if (long_rows && lane == 0) {
         long_rows[atomicAdd(n_long, 1)] = I;
       }
@@ -568,23 +587,32 @@ amg_status galerkin_group(const int *rp, const int *ci, const double *val, int n
   CWM_TRY(exclusive_scan(work.cnt, work.rpu, nc, work.scan, s));
   const int block = kWarpsPerBlock * 32;
   const int grid = grid_for((long long)nc * 16, block, num_sms() * 8);
+  // 32-bit sort keys (J << 8) | slot when every J leaves the all-ones key free for padding and
+  // the fine rows are long enough for coarse rows to reach the sort path (2 x mean > 32).
+  // Measured (elasticity 64^3, 78 entries per row): level-0 sweeps 2001 -> 1243 and 963 ->
+  // 586 us, setup 15.1 -> 13.6 ms; on the 7-entry rows of 3D Poisson 128^3, where the register
+  // path does the work, that kernel variant was 4% slower (its registers capped lower).
+  const double mean_row = work.n_fine > 0 ? (double)work.nnz_fine / work.n_fine : 0.0;
+  const bool k32 = CWM_GALERKIN_KEY32 && nc < (1 << 24) - 1 && mean_row > 16.0;
+#define CWM_GAL_LAUNCH(ACC)                                                                                     \
+  if (k32)                                                                                                     \
+    k_galerkin_warp<ACC, true><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,        \
+                                                      work.ci_pad, work.val_pad, diag_c, work.long_rows,        \
+                                                      work.n_long, d_err);                                      \
+  else                                                                                                         \
+    k_galerkin_warp<ACC, false><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,       \
+                                                       work.ci_pad, work.val_pad, diag_c, work.long_rows,       \
+                                                       work.n_long, d_err);                                     \
+  CWM_LAUNCH();                                                                                                \
+  k_galerkin_block<ACC><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(                                    \
+      rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu, work.ci_pad, work.val_pad, diag_c, dl1_c, work.long_rows, \
+      work.n_long, d_err);
   if (fp32) {
-    k_galerkin_warp<float><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
-                                                        work.ci_pad, work.val_pad, diag_c, work.long_rows,
-                                                        work.n_long, d_err);
-    CWM_LAUNCH();
-    k_galerkin_block<float><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
-        rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu, work.ci_pad, work.val_pad, diag_c, dl1_c,
-        work.long_rows, work.n_long, d_err);
+    CWM_GAL_LAUNCH(float)
   } else {
-    k_galerkin_warp<double><<<grid, block, 0, s>>>(nc, rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu,
-                                                         work.ci_pad, work.val_pad, diag_c, work.long_rows,
-                                                         work.n_long, d_err);
-    CWM_LAUNCH();
-    k_galerkin_block<double><<<num_sms() * 2, kLongThreads, kBlockCap * 8, s>>>(
-        rp, ci, val, m1, m2, agg, p, work.cnt, work.rpu, work.ci_pad, work.val_pad, diag_c, dl1_c,
-        work.long_rows, work.n_long, d_err);
+    CWM_GAL_LAUNCH(double)
   }
+#undef CWM_GAL_LAUNCH
   CWM_LAUNCH();
   return exclusive_scan(work.cnt, rpc, nc, work.scan, s);
 }

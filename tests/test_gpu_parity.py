@@ -146,13 +146,15 @@ def test_galerkin_long_rows_block_path():
     assert bits_equal(host(valc), valc_r)
 
 
-def _graded_graph(seed=11):
+def _graded_graph(seed=11, sparse_rows=0):
     """Random s.p.d. graph made of diagonal blocks of growing density (mean degrees 4 to
     ~200) joined by a few edges, so that the coarse rows of a pairwise aggregation gather
     from under 16 to over 256 fine entries."""
     rng = np.random.default_rng(seed)
     import scipy.sparse as sp
     blocks = [(3000, 4), (1000, 12), (600, 25), (400, 50), (400, 100), (500, 220)]
+    if sparse_rows:  # a sparse block that takes the mean row below 16
+        blocks = [(sparse_rows, 2)] + blocks
     rows, cols, base = [], [], 0
     for nb, deg in blocks:
         m = nb * deg // 2
@@ -173,12 +175,17 @@ def _graded_graph(seed=11):
     return A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64)
 
 
+@pytest.mark.parametrize("sparse_rows", [0, 20000])
 @pytest.mark.parametrize("fp32", [0, 1])
-def test_galerkin_all_row_paths(fp32):
+def test_galerkin_all_row_paths(fp32, sparse_rows):
     """Coarse rows of every length class -- registers (<= 16, <= 32 entries), the warp's
     register sort with 2, 4 and 8 keys per lane (<= 64, <= 128, <= 256) and the block kernel
-    (> 256) -- against the oracle, bit for bit (float64 and binary32 products)."""
-    mat = _graded_graph()
+    (> 256) -- against the oracle, bit for bit (float64 and binary32 products).  The fine
+    mean row is ~35 without the sparse block (the sort on 32-bit keys) and ~10 with it
+    (64-bit keys)."""
+    mat = _graded_graph(sparse_rows=sparse_rows)
+    lens0 = np.diff(mat[0])
+    assert (lens0.mean() > 16) == (sparse_rows == 0)
     n = len(mat[0]) - 1
     v = np.ones(n)
     w = oracle.edge_weights(*mat, v)
