@@ -222,8 +222,8 @@ amg_status block3_resid_restrict(const Sell3View<V> &A, int nc, const int *mptr,
 
 // ------------------------------------------------------------ FCG SpMV + dots ----
 // v = A w with the partial sums of w.r, w.v and w.q (q may be NULL) of Algorithm 3; the
-// last block turns every block's partials into the FCG scalars (fcg_scalars_from).  A block
-// of 256 threads takes 8 slices at a time, grid-stride.
+// last block turns every block's partials into the FCG scalars (fcg_scalars_from).  Each
+// warp takes a contiguous range of slices (below).
 __global__ void __launch_bounds__(kS3DotsBlock, CWM_B3_DOTS_MIN_BLOCKS)
     k_block3_spmv_dots(Sell3View<double> A, const double *__restrict__ w, const double *__restrict__ r,
                        const double *__restrict__ q, double *__restrict__ v, double *__restrict__ part, double *scal,
@@ -232,8 +232,15 @@ __global__ void __launch_bounds__(kS3DotsBlock, CWM_B3_DOTS_MIN_BLOCKS)
   const int nsl = (A.nbr + kS3 - 1) / kS3;
   const int lane = threadIdx.x & 31;
   double sa = 0.0, sb = 0.0, sg = 0.0;
-  for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl;
-       sl += ((long long)gridDim.x * blockDim.x) >> 5) {
+  // One resident wave (the grid is capped at the blocks that fit at once); warp g of W
+  // takes the contiguous slices [g nsl / W, (g+1) nsl / W), so every SM gets the same
+  // number of slices to within one per warp.  A grid of one slice per warp ran 3.3 waves,
+  // the last a third full, and left FP64 issue idle on most SMs at the end (145.4 against
+  // 142.9 us on Q1 elasticity 64^3).
+  const long long W = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long sl_end = (g + 1) * nsl / W;
+  for (long long sl = g * nsl / W; sl < sl_end; ++sl) {
     const int br = (int)(sl * kS3 + lane);
     const bool in = br < A.nbr;
     const int s0 = A.sptr[sl];
@@ -269,7 +276,7 @@ int block3_dots_blocks(int n) {
 amg_status block3_spmv_dots(const Sell3View<double> &A, const double *w, const double *r, const double *q, double *v,
                             double *part, int part_blocks, double *scal, unsigned *tick, int first, cudaStream_t s) {
   CWM_TRACE("spmv_dots_b3", 76.0 * A.nblocks + 4.0 * A.nbr + (q ? 32.0 : 24.0) * A.n, s);
-  int grid = block3_dots_blocks(A.n);
+  int grid = wave_cap(k_block3_spmv_dots, block3_dots_blocks(A.n), kS3DotsBlock);
   if (grid > part_blocks) grid = part_blocks;
   if (grid < 1) grid = 1;
   CWM_CUDA(launch_pdl(k_block3_spmv_dots, grid, kS3DotsBlock, 0, s, A, w, r, q, v, part, scal, tick, first));
