@@ -288,6 +288,19 @@ int64_t amg_launch_count(void);
  * output), CUDA.  Synchronises. */
 amg_status cwm_fp64_rates(double *fma_per_s, double *div_per_s, void *stream);
 
+/* Self-check of the edge weights' quotient (Sec. 2.2: c = 1 - num / den is evaluated with a
+ * correctly rounded division that runs on the integer pipes, not on the FP64 pipe).  For
+ * i = 0 .. n-1 the device derives an operand pair (x_i, y_i) from (seed, i) by splitmix64 --
+ * raw bit patterns (zeros, subnormals, infinities, NaNs), nearby exponents, quotients next
+ * to rounding boundaries (x = RN(y q)), powers of two, equal and extreme significands, and
+ * exponents at the edges of the normal range -- and compares the bits of that quotient with
+ * the hardware's IEEE division.  *mismatches: pairs whose bits differ (0 expected);
+ * *first: the smallest such i, or -1.  Host pointers.  Ordered on `stream`; allocates 16
+ * bytes of device memory.  Errors: INVALID_ARG (NULL output, n < 0), CUDA.  Synchronises.
+ * The paper has no counterpart. */
+amg_status cwm_div_check(long long n, unsigned long long seed, long long *mismatches, long long *first,
+                         void *stream);
+
 /* Human-readable name of a status, and the last error message of the calling thread. */
 const char *amg_status_string(amg_status s);
 const char *amg_last_error(void);

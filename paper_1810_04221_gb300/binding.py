@@ -25,7 +25,7 @@ EXPORTS = (
     "amg_num_levels", "amg_level_info", "amg_level_export", "amg_sweep_mate", "cwm_edge_weights",
     "cwm_suitor_match", "cwm_aggregate", "cwm_galerkin", "amg_status_string", "amg_last_error",
     "amg_trace_enable", "amg_trace_reset", "amg_trace_count", "amg_trace_get", "amg_launch_count",
-    "cwm_suitor_match_noalloc", "cwm_pattern_outer", "cwm_fp64_rates",
+    "cwm_suitor_match_noalloc", "cwm_pattern_outer", "cwm_fp64_rates", "cwm_div_check",
 )
 
 
@@ -118,6 +118,7 @@ def load(path: str | None = None):
             "amg_trace_get": (i, [vp, i, C.POINTER(AmgTraceEntry)]),
             "amg_launch_count": (i64, []),
             "cwm_fp64_rates": (i, [C.POINTER(d), C.POINTER(d), vp]),
+            "cwm_div_check": (i, [C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), vp]),
             "amg_status_string": (C.c_char_p, [i]),
             "amg_last_error": (C.c_char_p, []),
         }
@@ -368,3 +369,12 @@ def cwm_fp64_rates(stream=None) -> tuple[float, float]:
     f, d = C.c_double(), C.c_double()
     _check(load().cwm_fp64_rates(C.byref(f), C.byref(d), _stream(stream)), "cwm_fp64_rates")
     return f.value, d.value
+
+
+def cwm_div_check(n: int, seed: int, stream=None) -> tuple[int, int]:
+    """(mismatching pairs, first mismatching index or -1) of the edge weights' integer-pipe
+    quotient against the hardware division over n generated operand pairs."""
+    mm, first = C.c_longlong(), C.c_longlong()
+    _check(load().cwm_div_check(int(n), int(seed) & (2**64 - 1), C.byref(mm), C.byref(first), _stream(stream)),
+           "cwm_div_check")
+    return mm.value, first.value

@@ -2,6 +2,7 @@
 // (Sec. 2.2), Suitor matching (Sec. 3.1), aggregation (Sec. 2.2, Algorithm 2), the
 // orthonormal prolongator (Sec. 2.2), and the composition of sweeps (Sec. 5).
 #include "coarsen.cuh"
+#include "divint.cuh"
 
 namespace cwm {
 
@@ -80,7 +81,8 @@ amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, 
 // ------------------------------------------------------------ edge weights ----
 // Sec. 2.2, C(A, v).  No FMA: every product and sum is an explicit round-to-nearest
 // intrinsic in the order ((2 a) v_a) v_b over ((a_aa v_a) v_a) + ((a_bb v_b) v_b),
-// a = min(i,j).
+// a = min(i,j).  The quotient is the correctly rounded one, formed on the integer pipes
+// (div_rn_int), which leaves five binary64 operations per edge on the scarce FP64 pipe.
 //
 // Row blocks, evaluating each edge once.  A block of kWB
 // threads owns kWB consecutive rows.  Each row's thread finds where its upper part
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kWB) k_edge_weights_rb(int n, const int *__res
         const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a[e]), va), vb);
         const double den = __dadd_rn(s_d[il], __ldg(dv + j));
         if (nonzero_f64(den)) {
-          const double cc = __dsub_rn(1.0, __ddiv_rn(num, den));
+          const double cc = __dsub_rn(1.0, div_rn_int(num, den));
           if (pos_f64(cc)) c = cc;
         }
       }

@@ -66,6 +66,16 @@ def test_edge_weights_bit_exact(case):
     assert bits_equal(got, ref)
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_weight_quotient_matches_hardware_division(seed):
+    """The edge weights divide on the integer pipes; that quotient is bit-identical to the
+    IEEE division on 2^24 generated operand pairs per seed (raw bit patterns, nearby
+    exponents, quotients next to rounding boundaries, powers of two, extreme significands,
+    exponents at the edges of the normal range)."""
+    mismatches, first = B.cwm_div_check(1 << 24, seed)
+    assert (mismatches, first) == (0, -1)
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_suitor_matches_greedy_bit_exact(case):
     name, mat, v = case
