@@ -12,9 +12,9 @@ FP64 setup, FP32 V-cycle inside the FP64 FCG, rtol 1e-8.  The all-FP64 run of th
 workload is timed beside it (`variants`).
 
 Prints ONE JSON line (rank 0).  `value` is milliseconds per step (setup + solve) with the
-inputs already resident in HBM; `e2e` times the same C-ABI calls with host buffers
-(pinned host -> device copies of the CSR, v and b, and the device -> host copy of x inside
-the timed region).  `--impl reference` times the CPU FP64 oracle (the reference arm).
+inputs already resident in HBM; `e2e` times the same C-ABI calls made on pinned host
+arrays (amg_setup reads the CSR and v from host memory, amg_pcg_solve reads b and the
+initial guess and writes x back, every transfer inside the timed region).  `--impl reference` times the CPU FP64 oracle (the reference arm).
 Under torchrun every rank runs an independent replica (the solver does not shard).
 """
 from __future__ import annotations
@@ -300,18 +300,18 @@ def run_cuda(args, rank, world, dist):
             print(json.dumps({"profile_run": True, "ms_per_step": round(ms_per_step, 3), "dominant": dominant}))
         return
 
-    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    # e2e through the C ABI with host buffers (pinned): amg_setup reads the CSR and v from
+    # host memory, amg_pcg_solve reads b and the zero initial guess and writes x back, all
+    # inside the timed region (the library moves page-locked arrays with its own copy kernel)
     h_rp, h_ci, h_val, h_v, h_b = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (rp, ci, val, v, b))
     h_x = torch.empty(n, dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_ci, h_val, h_v, h_b))
+    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_ci, h_val, h_v, h_b, h_x))
     d2h = h_x.numel() * h_x.element_size()
 
     def e2e_step():
-        g = [t.cuda(non_blocking=True) for t in (h_rp, h_ci, h_val, h_v, h_b)]
-        hh = B.amg_setup(g[0], g[1], g[2], g[3], params())
-        xx = torch.zeros(n, dtype=torch.float64, device="cuda")
-        B.amg_pcg_solve(hh, g[4], xx, rtol=args.rtol, itmax=args.itmax)
-        h_x.copy_(xx, non_blocking=True)
+        hh = B.amg_setup(h_rp, h_ci, h_val, h_v, params())
+        h_x.zero_()
+        B.amg_pcg_solve(hh, h_b, h_x, rtol=args.rtol, itmax=args.itmax)
         torch.cuda.current_stream().synchronize()
         hh.free()
 
@@ -330,14 +330,20 @@ def run_cuda(args, rank, world, dist):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
     e2e_steps = [round(es[k].elapsed_time(es[k + 1]), 3) for k in range(args.steps)]
-    # the host -> device copies of one step alone (what e2e adds to the device-resident step)
-    c0 = torch.cuda.Event(enable_timing=True)
-    c1 = torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    g_copy = [t.cuda(non_blocking=True) for t in (h_rp, h_ci, h_val, h_v, h_b)]
-    c1.record(stream)
-    torch.cuda.synchronize()
-    h2d_ms = c0.elapsed_time(c1)
+    # the host -> device copies of one step alone (what e2e adds to the device-resident
+    # step), done the way the library does them (cwm_copy); best of three
+    g_copy = [torch.empty_like(t, device="cuda") for t in (h_rp, h_ci, h_val, h_v, h_b, h_x)]
+    h2d_times = []
+    for _ in range(3):
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for dst, src in zip(g_copy, (h_rp, h_ci, h_val, h_v, h_b, h_x)):
+            B.cwm_copy(dst, src)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        h2d_times.append(c0.elapsed_time(c1))
+    h2d_ms = min(h2d_times)
     del g_copy
 
     # roofline of the dominant kernel class over the timed region

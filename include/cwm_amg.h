@@ -129,12 +129,15 @@ void amg_default_params(amg_params *p);
 
 /* Builds the hierarchy {A^k, P^k, v^k} of Sec. 2.1 by Sec. 2.2/3.1 coarsening.
  *   n, nnz          size of A (n >= 1, 0 <= nnz < 2^31)
- *   d_row_ptr/col/val  CSR of A (device).  A must be structurally and numerically
+ *   d_row_ptr/col/val  CSR of A.  A must be structurally and numerically
  *                   (bit-for-bit) symmetric with positive diagonal entries.
- *   d_v             smooth vector (device, n doubles) driving the weights and P.
+ *   d_v             smooth vector (n doubles) driving the weights and P.
  *   params          NULL = defaults.
  *   out             receives the handle (NULL on failure).
- * The inputs are copied; the caller may free them on return.  Synchronises.
+ * Each of the four input arrays may be device memory or host memory.  Page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister, a pinned framework tensor) is read by the
+ * library's copy kernel through its device mapping; pageable host memory is copied with
+ * cudaMemcpyAsync.  The inputs are copied; the caller may free them on return.  Synchronises.
  * Errors: INVALID_ARG (sizes, NULL, malformed or non-symmetric CSR when check_input),
  * NOT_SPD (diagonal missing or <= 0), OOM, CUDA, TIMEOUT. */
 amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
@@ -146,7 +149,11 @@ amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t
 amg_status amg_vcycle(amg_handle h, const double *d_r, double *d_w, void *stream);
 
 /* Flexible CG (Algorithm 3) preconditioned by amg_vcycle for A x = b.
- *   d_b     device, n doubles.   d_x  device, n doubles: initial guess in, solution out.
+ *   d_b     n doubles.   d_x  n doubles: initial guess in, solution out.
+ *           Each may be device or host memory (page-locked or pageable, as for
+ *           amg_setup); host arrays are solved through device copies that the handle
+ *           keeps, and a host x is written back before the call returns (also on
+ *           NOT_CONVERGED and BREAKDOWN; on other errors its contents are unspecified).
  *   rtol    stop once ||r||/||b|| <= rtol (recursive residual).   itmax >= 0.
  *   info    may be NULL; else receives iterations, residuals and timings.
  * Synchronises (the host reads ||r|| once per iteration).
@@ -287,6 +294,17 @@ int64_t amg_launch_count(void);
  * a few milliseconds and allocates 8 bytes of device memory.  Errors: INVALID_ARG (NULL
  * output), CUDA.  Synchronises. */
 amg_status cwm_fp64_rates(double *fma_per_s, double *div_per_s, void *stream);
+
+/* Copies `bytes` bytes between device memory and device or host memory, the way amg_setup
+ * and amg_pcg_solve move host arrays: page-locked host memory by an SM copy kernel through
+ * its device mapping (on GB300 the copy engines' host-to-device transfers stalled for tens of
+ * milliseconds about every half second; the kernel's did not), pageable host memory by
+ * cudaMemcpyAsync (the call then waits for it), device to device by cudaMemcpyAsync.  At
+ * least one of dst, src must be device memory (bytes = 0 does nothing and accepts any
+ * pointers); the ranges must not overlap.  Ordered on
+ * `stream`.  Errors: INVALID_ARG (NULL pointer, bytes < 0, no device side), CUDA.  The
+ * paper has no counterpart. */
+amg_status cwm_copy(void *dst, const void *src, int64_t bytes, void *stream);
 
 /* Self-check of the edge weights' quotient (Sec. 2.2: c = 1 - num / den is evaluated with a
  * correctly rounded division that runs on the integer pipes, not on the FP64 pipe).  For

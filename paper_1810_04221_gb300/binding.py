@@ -25,7 +25,7 @@ EXPORTS = (
     "amg_num_levels", "amg_level_info", "amg_level_export", "amg_sweep_mate", "cwm_edge_weights",
     "cwm_suitor_match", "cwm_aggregate", "cwm_galerkin", "amg_status_string", "amg_last_error",
     "amg_trace_enable", "amg_trace_reset", "amg_trace_count", "amg_trace_get", "amg_launch_count",
-    "cwm_suitor_match_noalloc", "cwm_pattern_outer", "cwm_fp64_rates", "cwm_div_check",
+    "cwm_suitor_match_noalloc", "cwm_pattern_outer", "cwm_fp64_rates", "cwm_div_check", "cwm_copy",
 )
 
 
@@ -119,6 +119,7 @@ def load(path: str | None = None):
             "amg_launch_count": (i64, []),
             "cwm_fp64_rates": (i, [C.POINTER(d), C.POINTER(d), vp]),
             "cwm_div_check": (i, [C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), vp]),
+            "cwm_copy": (i, [vp, vp, i64, vp]),
             "amg_status_string": (C.c_char_p, [i]),
             "amg_last_error": (C.c_char_p, []),
         }
@@ -163,6 +164,19 @@ def _dev(t: torch.Tensor | None, dtype: torch.dtype, name: str, numel: int | Non
     return C.c_void_p(t.data_ptr())
 
 
+def _buf(t: torch.Tensor | None, dtype: torch.dtype, name: str, numel: int | None = None):
+    """A device or host (pinned or pageable) tensor for the calls that accept either."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor (got {t.dtype})")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements (got {t.numel()})")
+    return C.c_void_p(t.data_ptr())
+
+
 def amg_default_params(**overrides) -> AmgParams:
     p = AmgParams()
     load().amg_default_params(C.byref(p))
@@ -193,8 +207,8 @@ def amg_setup(row_ptr, col, val, v, params: AmgParams | None = None, stream=None
     n = row_ptr.numel() - 1
     nnz = col.numel()
     out = C.c_void_p()
-    st = load().amg_setup(n, nnz, _dev(row_ptr, torch.int32, "row_ptr"), _dev(col, torch.int32, "col"),
-                          _dev(val, torch.float64, "val", nnz), _dev(v, torch.float64, "v", n),
+    st = load().amg_setup(n, nnz, _buf(row_ptr, torch.int32, "row_ptr"), _buf(col, torch.int32, "col"),
+                          _buf(val, torch.float64, "val", nnz), _buf(v, torch.float64, "v", n),
                           C.byref(params) if params is not None else None, _stream(stream), C.byref(out))
     _check(st, "amg_setup")
     return AmgHandle(out.value, n, nnz)
@@ -213,7 +227,7 @@ def amg_vcycle(h: AmgHandle, r, w, stream=None):
 def amg_pcg_solve(h: AmgHandle, b, x, rtol: float = 1e-8, itmax: int = 5000, stream=None):
     """Returns (status, info dict); NOT_CONVERGED is returned, other errors raise."""
     info = AmgInfo()
-    st = load().amg_pcg_solve(C.c_void_p(h.ptr), _dev(b, torch.float64, "b", h.n), _dev(x, torch.float64, "x", h.n),
+    st = load().amg_pcg_solve(C.c_void_p(h.ptr), _buf(b, torch.float64, "b", h.n), _buf(x, torch.float64, "x", h.n),
                               float(rtol), int(itmax), _stream(stream), C.byref(info))
     _check(st, "amg_pcg_solve", allow=(AMG_OK, AMG_ERR_NOT_CONVERGED))
     return st, info.as_dict()
@@ -369,6 +383,16 @@ def cwm_fp64_rates(stream=None) -> tuple[float, float]:
     f, d = C.c_double(), C.c_double()
     _check(load().cwm_fp64_rates(C.byref(f), C.byref(d), _stream(stream)), "cwm_fp64_rates")
     return f.value, d.value
+
+
+def cwm_copy(dst: torch.Tensor, src: torch.Tensor, stream=None):
+    """dst <- src (same byte size; at least one of them on the device), as the library moves
+    host arrays."""
+    nb = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() < nb or not (dst.is_contiguous() and src.is_contiguous()):
+        raise ValueError("cwm_copy: dst must be contiguous and at least as large as src")
+    _check(load().cwm_copy(C.c_void_p(dst.data_ptr()), C.c_void_p(src.data_ptr()), nb, _stream(stream)), "cwm_copy")
+    return dst
 
 
 def cwm_div_check(n: int, seed: int, stream=None) -> tuple[int, int]:

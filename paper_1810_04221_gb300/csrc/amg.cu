@@ -164,6 +164,7 @@ struct amg_hierarchy {
   Mailbox box;
   // FCG vectors and reductions
   DBuf<double> r, w, d, vv, q, part, part2, scal;
+  DBuf<double> bdev, xdev;  // device copies of a solve's host b and x (amg_pcg_solve)
   DBuf<unsigned> tick;  // last-block tickets of the fused reductions (kept at zero between launches)
   double t_setup_ms = 0.0, t_solve_ms = 0.0;
   Tracer trace;
@@ -987,12 +988,13 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   CWM_TRY(L0.v.alloc(n, s));
   CWM_TRY(L0.diag.alloc(n, s));
   CWM_TRY(L0.dl1.alloc(n, s));
-  CWM_CUDA(cudaMemcpyAsync(L0.rp.get(), rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+  // the inputs may be device, page-locked host or pageable host memory (copy_in)
+  CWM_TRY(copy_in(L0.rp.get(), rp, sizeof(int) * ((size_t)n + 1), s));
   if (nnz) {
-    CWM_CUDA(cudaMemcpyAsync(L0.ci.get(), ci, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
-    CWM_CUDA(cudaMemcpyAsync(L0.val.get(), val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
+    CWM_TRY(copy_in(L0.ci.get(), ci, sizeof(int) * (size_t)nnz, s));
+    CWM_TRY(copy_in(L0.val.get(), val, sizeof(double) * (size_t)nnz, s));
   }
-  CWM_CUDA(cudaMemcpyAsync(L0.v.get(), v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  CWM_TRY(copy_in(L0.v.get(), v, sizeof(double) * (size_t)n, s));
   if (P.check_input) {
     CWM_TRY(check_input(n, nnz, L0.rp.get(), L0.ci.get(), L0.val.get(), true, h->err.get(), s));
     CWM_TRY(read_err(h, "amg_setup (input check)"));
@@ -1322,6 +1324,21 @@ extern "C" amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x
   const CsrView<double> A = L0.view64();
   const int n = L0.n;
   const int nb = fcg_partial_blocks(n);
+  // b and x in host memory are solved through device copies owned by the handle (so the
+  // iteration graphs captured for them stay valid from call to call); x is copied back
+  // before the call returns
+  double *const x_user = d_x;
+  const bool x_host = mem_kind(d_x, nullptr) != MemKind::kDevice;
+  if (mem_kind(d_b, nullptr) != MemKind::kDevice) {
+    if (!h->bdev.get()) CWM_TRY(h->bdev.alloc(n, s));
+    CWM_TRY(copy_in(h->bdev.get(), d_b, sizeof(double) * (size_t)n, s));
+    d_b = h->bdev.get();
+  }
+  if (x_host) {
+    if (!h->xdev.get()) CWM_TRY(h->xdev.alloc(n, s));
+    CWM_TRY(copy_in(h->xdev.get(), x_user, sizeof(double) * (size_t)n, s));
+    d_x = h->xdev.get();
+  }
   double *scal = h->scal.get();
   CWM_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * kFcgSlots, s));
   CWM_TRY(residual(A, d_b, d_x, h->r.get(), s));
@@ -1366,6 +1383,7 @@ extern "C" amg_status amg_pcg_solve(amg_handle h, const double *d_b, double *d_x
   CWM_TRY(sqnorm_partials(n, h->vv.get(), h->part2.get(), s));
   CWM_TRY(reduce_into(nb, h->part2.get(), scal, kBB, s));  // slot reused: true ||r||^2
   CWM_CUDA(cudaMemcpyAsync(h->box.dbls + 12, scal + kBB, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (x_host) CWM_TRY(copy_out(x_user, d_x, sizeof(double) * (size_t)n, s));
   CWM_CUDA(cudaStreamSynchronize(s));
   CWM_CUDA(cudaEventRecord(h->ev_out, s));
   CWM_CUDA(cudaStreamWaitEvent(user, h->ev_out, 0));

@@ -169,6 +169,17 @@ struct DBuf {
 // Makes the device's default memory pool keep freed memory (repeated setups reuse it).
 void retain_pool_memory();
 
+// ---------------------------------------------------------------- host arrays ----
+// Where a caller's pointer lives: device (or managed) memory, page-locked host memory
+// (with its device alias), or pageable host memory.
+enum class MemKind { kDevice, kPinned, kPageable };
+MemKind mem_kind(const void *p, void **dev_alias);
+// bytes from src (device, page-locked or pageable host) into device memory d_dst, and from
+// device memory d_src out to dst, ordered on s; page-locked host memory is moved by an SM
+// kernel through its device mapping, pageable memory by cudaMemcpyAsync (which waits).
+amg_status copy_in(void *d_dst, const void *src, size_t bytes, cudaStream_t s);
+amg_status copy_out(void *dst, const void *d_src, size_t bytes, cudaStream_t s);
+
 // ---------------------------------------------------------------- launch ----
 int num_sms();
 // Grid for `items` work items of `per_block` items each, capped at `waves` full waves.
