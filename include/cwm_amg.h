@@ -193,7 +193,10 @@ amg_status amg_sweep_mate(amg_handle h, int level, int sweep, int32_t *d_mate, i
 /* Edge weights (Sec. 2.2, C(A, v)): for every stored slot k of row i with column j,
  *   d_w[k] = 1 - 2 a_ab v_a v_b / (a_aa v_a^2 + a_bb v_b^2),  a = min(i,j), b = max(i,j),
  * evaluated without FMA as ((2 a_ab) v_a) v_b over ((a_aa v_a) v_a) + ((a_bb v_b) v_b);
- * 0 on the diagonal, on stored zeros and where the weight is not positive.
+ * 0 on the diagonal, on stored zeros and where the weight is not positive.  A must be
+ * symmetric, as for amg_setup (operators of short rows evaluate each edge once and copy
+ * it to the mirror slot; long-row operators evaluate every slot from its own value).
+ * The quotient is the correctly rounded one, formed on the integer pipes (cwm_div_check).
  * d_w: device, nnz doubles.  Errors: INVALID_ARG, NOT_SPD.  Synchronises. */
 amg_status cwm_edge_weights(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
                             const double *d_val, const double *d_v, double *d_w, void *stream);

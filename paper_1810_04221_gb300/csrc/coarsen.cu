@@ -92,6 +92,19 @@ amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, 
 // whole-warp instructions at a low rate on GB300 -- runs on full warps.  The thread that
 // evaluates slot (i, j) also stores the weight into the mirror slot (j, i), found by a
 // binary search in row j.
+// 2 a, exactly: the exponent field incremented when a is normal and 2 a finite (no FP64
+// instruction), else the multiply.
+__device__ __forceinline__ double twice_f64(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const unsigned e = (unsigned)((b >> 52) & 0x7ff);
+  return e - 1u < 2045u ? __longlong_as_double((long long)(b + (1ull << 52))) : __dmul_rn(2.0, a);
+}
+// Operators whose rows average more than this many stored slots take k_edge_weights_all
+// (every slot from its own row: twice the FP64 work, no mirror searches), the others
+// k_edge_weights_rb.  Measured on GB300: elasticity levels (78 to a few hundred slots per
+// row) 2.69 -> 2.35 ms of weights per setup; Poisson and lognormal (7 to 27 per row) lost
+// 25% and 16% with every slot evaluated.
+constexpr double kWeightsAllMean = 32.0;
 constexpr int kWB = 256;
 constexpr int kWE = 8;
 constexpr int kWC = kWB * kWE;
@@ -171,7 +184,7 @@ __global__ void __launch_bounds__(kWB) k_edge_weights_rb(int n, const int *__res
       double c = 0.0;
       if (nonzero_f64(a[e])) {
         const double va = s_v[il], vb = __ldg(v + j);
-        const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a[e]), va), vb);
+        const double num = __dmul_rn(__dmul_rn(twice_f64(a[e]), va), vb);
         const double den = __dadd_rn(s_d[il], __ldg(dv + j));
         if (nonzero_f64(den)) {
           const double cc = __dsub_rn(1.0, div_rn_int(num, den));
@@ -195,6 +208,68 @@ __global__ void __launch_bounds__(kWB) k_edge_weights_rb(int n, const int *__res
   }
 }
 
+// Every stored slot evaluated from its own row's value: no mirror-slot search, every slot
+// written (the diagonal and ineligible slots with 0), and the weights are those of the
+// definition slot by slot even where the values are not symmetric.  A block owns kWB
+// consecutive rows, whose slots are contiguous; each chunk of kWC of them is spread over the
+// block's threads (kWE per thread, full warps) with the slot's row taken from a shared map.
+__global__ void __launch_bounds__(kWB) k_edge_weights_all(int n, const int *__restrict__ rp,
+                                                          const int *__restrict__ ci,
+                                                          const double *__restrict__ val,
+                                                          const double *__restrict__ dv,
+                                                          const double *__restrict__ v,
+                                                          double *__restrict__ w) {
+  __shared__ double s_v[kWB], s_d[kWB];
+  __shared__ int s_rs[kWB + 1];
+  __shared__ unsigned char s_row[kWC];
+  const int t = threadIdx.x;
+  const int r0 = blockIdx.x * kWB;
+  const int nrows = min(kWB, n - r0);
+  const int base = rp[r0];
+  if (t < nrows) {
+    s_v[t] = v[r0 + t];
+    s_d[t] = dv[r0 + t];
+    s_rs[t] = rp[r0 + t] - base;
+  }
+  if (t == 0) s_rs[nrows] = rp[r0 + nrows] - base;
+  __syncthreads();
+  const int U = s_rs[nrows];
+  const int my_s = t < nrows ? s_rs[t] : 0, my_e = t < nrows ? s_rs[t + 1] : 0;
+  for (int c0 = 0; c0 < U; c0 += kWC) {
+    const int cend = min(c0 + kWC, U);
+    for (int q = max(my_s, c0); q < min(my_e, cend); ++q) s_row[q - c0] = (unsigned char)t;
+    __syncthreads();
+    int col[kWE];
+    double a[kWE];
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      const int q = c0 + e * kWB + t;
+      col[e] = q < cend ? __ldg(ci + base + q) : 0;
+      a[e] = q < cend ? __ldg(val + base + q) : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      const int q = c0 + e * kWB + t;
+      if (q >= cend) continue;
+      const int il = s_row[q - c0];
+      const int i = r0 + il, j = col[e];
+      double c = 0.0;
+      if (j != i && nonzero_f64(a[e])) {
+        const double vi = s_v[il], vj = __ldg(v + j), di = s_d[il], dj = __ldg(dv + j);
+        const bool lo = i < j;  // the smaller index's values come first
+        const double num = __dmul_rn(__dmul_rn(twice_f64(a[e]), lo ? vi : vj), lo ? vj : vi);
+        const double den = __dadd_rn(lo ? di : dj, lo ? dj : di);
+        if (nonzero_f64(den)) {
+          const double cc = __dsub_rn(1.0, div_rn_int(num, den));
+          if (pos_f64(cc)) c = cc;
+        }
+      }
+      __stcs(w + base + q, c);
+    }
+    __syncthreads();
+  }
+}
+
 // dv[i] = (a_ii v_i) v_i: the per-vertex half of the denominator, rounded exactly as in
 // the per-slot expression, so that den = dv[a] + dv[b] is bit-identical.
 __global__ void k_vertex_dv(int n, const double *__restrict__ diag, const double *__restrict__ v,
@@ -213,8 +288,12 @@ amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, cons
   CWM_LAUNCH();
   // lower slots without an upper partner (a pattern that is not symmetric) stay 0; a
   // structurally symmetric pattern has every slot written, so the caller may skip this
-  if (clear) CWM_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)nnz, s));
-  k_edge_weights_rb<<<(n + kWB - 1) / kWB, kWB, 0, s>>>(n, rp, ci, val, dv_scratch, v, w);
+  if ((double)nnz > kWeightsAllMean * n) {
+    k_edge_weights_all<<<(n + kWB - 1) / kWB, kWB, 0, s>>>(n, rp, ci, val, dv_scratch, v, w);
+  } else {
+    if (clear) CWM_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)nnz, s));
+    k_edge_weights_rb<<<(n + kWB - 1) / kWB, kWB, 0, s>>>(n, rp, ci, val, dv_scratch, v, w);
+  }
   CWM_LAUNCH();
   return AMG_OK;
 }

@@ -50,9 +50,10 @@ __device__ __forceinline__ double div_rn_int(double x, double y) {
   const int lt = mx < my ? 1 : 0;
   int E = ex - ey + 1023 - lt;  // biased exponent of the quotient
   if (ex == 0 || ex == 0x7ff || ey == 0 || ey == 0x7ff || E < 1 || E > 2045) return __ddiv_rn(x, y);
-  // seed: 2^87 / (my >> 29) in binary32 (the top 24 bits of my, exactly representable)
-  const float s = __frcp_rn((float)(unsigned)(my >> 29)) * 0x1p87f;  // in (2^63, 2^64]
-  unsigned long long v = s >= 0x1p64f ? ~0ull : __float2ull_rz(s);
+  // seed: 2^87 / (my >> 29) from a binary32 reciprocal of the top 24 bits of my (exactly
+  // representable), taken to 32 bits (a 32-bit conversion: 64-bit ones are slow) and shifted
+  const float s = __frcp_rn((float)(unsigned)(my >> 29)) * 0x1p55f;  // in (2^31, 2^32]
+  unsigned long long v = (unsigned long long)(s >= 0x1p32f ? 0xffffffffu : __float2uint_rz(s)) << 32;
   const unsigned long long d = my << 10;
   v = divint_newton<42>(d, v);  // |e| < 2^104: the seed's relative error is below 2^-22
   v = divint_newton<21>(d, v);  // |e| < 2^83: below 2^-44 after the first step
