@@ -217,10 +217,20 @@ inline int tile_for_mean(double mean) {
 #ifndef CWM_TILE_MAX_PER_LANE
 #define CWM_TILE_MAX_PER_LANE 32
 #endif
+// The tile also gives each lane about CWM_TILE32_MEAN_PER_LANE entries of the mean row: the
+// row walk keeps a predicated group of four per lane in flight, so narrower tiles put more
+// rows in flight per warp.  Measured (binary32 cycles): 5 against ~1 (the earlier 4.5 /
+// 9 / 18 steps) took Q1 elasticity 64^3 59.5 -> 58.9 ms (level-1 residual 49.3 -> 43.1 us,
+// level-2 A P sweep 18.4 -> 14.3 us), lognormal 160^3 42.9 -> 41.4 ms, 3D Poisson 128^3
+// 15.7 -> 15.4 ms; 2.5 gained half as much.
+#ifndef CWM_TILE32_MEAN_PER_LANE
+#define CWM_TILE32_MEAN_PER_LANE 5.0
+#endif
 inline int tile_for_rows(double mean, int max_row) {
   const int e = CWM_TILE_MAX_PER_LANE;
   const int t_max = max_row <= 4 * e ? 4 : max_row <= 8 * e ? 8 : max_row <= 16 * e ? 16 : 32;
-  const int t_mean = tile_for_mean(mean);
+  int t_mean = 4;
+  while (t_mean < 32 && mean > CWM_TILE32_MEAN_PER_LANE * t_mean) t_mean <<= 1;
   return t_max > t_mean ? t_max : t_mean;
 }
 

@@ -20,11 +20,12 @@
 namespace cwm {
 
 constexpr int kSellWin = 256;  // rows sorted together (one block)
-// Entries per lane whose loads are in flight together in binary32 (4 in binary64): 16
-// measured 59.1 / 31.0 us on Q1 elasticity 64^3 levels 0 / 1 (A P), 8 gave 60.8 / 31.6, 4
-// gave 61.1 / 32.1.
+// Entries per lane whose loads are in flight together in binary32 (4 in binary64), in
+// predicated groups: 8 measured 50.8 / 22.9 us on Q1 elasticity 64^3 levels 0 / 1 (A P),
+// 16 gave 53.0 / 27.0 (56 registers); whole groups with a one-at-a-time remainder gave
+// 59.0 / 31.0 at 16.
 #ifndef CWM_SELL_UNROLL32
-#define CWM_SELL_UNROLL32 16
+#define CWM_SELL_UNROLL32 8
 #endif
 constexpr int kSellBlock = 128;
 
@@ -122,6 +123,27 @@ __device__ __forceinline__ V sell_row(const SellView<V> &A, long long base, int 
   constexpr int U = sizeof(V) == 4 ? CWM_SELL_UNROLL32 : 4;
   V acc = V(0);
   const int steps = L > j ? (L - j + K - 1) / K : 0;  // this lane's entries
+#if CWM_ROW_PRED
+  // groups of U entries, the last one's missing entries predicated off: a lane's row costs
+  // one round of loads per U entries (its remainder walked one entry per round trip before:
+  // 12 dependent gathers for a 44-entry row); products added in ascending entry order
+  for (int t = 0; t < steps; t += U) {
+    int c[U];
+    V a[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = t + u < steps;
+      c[u] = ok ? __ldcs(A.col + base + 32LL * (t + u)) : 0;
+      a[u] = ok ? __ldcs(A.val + base + 32LL * (t + u)) : V(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      xv[u] = t + u < steps ? (SCALED ? __ldg(d + c[u]) * __ldg(x + c[u]) : __ldg(x + c[u])) : V(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (t + u < steps) acc = fma(-a[u], xv[u], acc);
+  }
+#else
   int t = 0;
   for (; t + U <= steps; t += U) {
     int c[U];
@@ -141,6 +163,7 @@ __device__ __forceinline__ V sell_row(const SellView<V> &A, long long base, int 
     const V xv = SCALED ? __ldg(d + c) * __ldg(x + c) : __ldg(x + c);
     acc = fma(-__ldcs(A.val + base + 32LL * t), xv, acc);
   }
+#endif
 #pragma unroll
   for (int o = K / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, K);
   return init + acc;

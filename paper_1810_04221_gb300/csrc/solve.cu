@@ -25,8 +25,28 @@ __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int 
   auto xj = [&](int j) { return SCALED ? __ldg(d + j) * __ldg(x + j) : __ldg(x + j); };
   if (active && x) {
     const int b = rp[row], e = rp[row + 1];
+    // four entries per lane in flight, the last group's missing ones predicated off, so that
+    // a row of up to 4 T entries costs one round of loads (a long row is a chain of gathers
+    // otherwise; a row of 2-3 T entries walked one entry per round trip took three); each
+    // lane's products are added in ascending entry order
+#if CWM_ROW_PRED
+    for (int k = b + lane; k < e; k += 4 * T) {
+      int jj[4];
+      V aa[4], xx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = k + u * T < e;
+        jj[u] = ok ? ci[k + u * T] : 0;
+        aa[u] = ok ? val[k + u * T] : V(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xx[u] = k + u * T < e ? xj(jj[u]) : V(0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k + u * T < e) s = fma(sg * aa[u], xx[u], s);
+    }
+#else
     int k = b + lane;
-    // four entries per lane in flight: a long row is a chain of gathers otherwise
     for (; k + 3 * T < e; k += 4 * T) {
       const int j0 = ci[k], j1 = ci[k + T], j2 = ci[k + 2 * T], j3 = ci[k + 3 * T];
       const V a0 = val[k], a1 = val[k + T], a2 = val[k + 2 * T], a3 = val[k + 3 * T];
@@ -37,6 +57,7 @@ __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int 
       s = fma(sg * a3, x3, s);
     }
     for (; k < e; k += T) s = fma(sg * val[k], xj(ci[k]), s);
+#endif
   }
 #pragma unroll
   for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
@@ -1013,7 +1034,14 @@ amg_status dense_coarse_build(const CsrView<double> &A, const double *dinv, int 
   return AMG_OK;
 }
 
-// y = X b, one warp per row of X (row-major)
+// y = X b, one warp per row of X (row-major).  Each lane keeps kDenseAcc partial sums over
+// the columns lane + 32 (kDenseAcc m + k), so that kDenseAcc loads of the row are in flight
+// together (one load per round trip made the 832-row coarsest operator of elasticity take
+// 14 us), then adds them in k order and the warp in a fixed shuffle order.
+#ifndef CWM_DENSE_ACC
+#define CWM_DENSE_ACC 8
+#endif
+constexpr int kDenseAcc = CWM_DENSE_ACC;
 template <class V>
 __global__ void k_dense_matvec(int n, const V *__restrict__ X, const V *__restrict__ b, V *__restrict__ y) {
   pdl_begin();
@@ -1022,11 +1050,26 @@ __global__ void k_dense_matvec(int n, const V *__restrict__ X, const V *__restri
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long i = warp; i < n; i += nw) {
     const V *row = X + i * n;
-    V acc = V(0);
-    for (int c = lane; c < n; c += 32) acc = fma(row[c], b[c], acc);
+    V acc[kDenseAcc];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) y[i] = acc;
+    for (int k = 0; k < kDenseAcc; ++k) acc[k] = V(0);
+    for (int c0 = 0; c0 < n; c0 += 32 * kDenseAcc) {
+      V xv[kDenseAcc], bv[kDenseAcc];
+#pragma unroll
+      for (int k = 0; k < kDenseAcc; ++k) {
+        const int c = c0 + 32 * k + lane;
+        xv[k] = c < n ? row[c] : V(0);
+        bv[k] = c < n ? b[c] : V(0);
+      }
+#pragma unroll
+      for (int k = 0; k < kDenseAcc; ++k) acc[k] = fma(xv[k], bv[k], acc[k]);
+    }
+    V a = acc[0];
+#pragma unroll
+    for (int k = 1; k < kDenseAcc; ++k) a += acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) y[i] = a;
   }
 }
 
@@ -1113,7 +1156,10 @@ int fcg_partial_blocks(int n) {
   const int cap = num_sms() * kDotsBlocksPerSm;
   return rb < cap ? rb : cap;
 }
-constexpr int kUpdChunk = 8 * kRB;  // entries per fcg_update block
+#ifndef CWM_UPD_STEPS
+#define CWM_UPD_STEPS 4
+#endif
+constexpr int kUpdChunk = 2 * CWM_UPD_STEPS * kRB;  // entries per fcg_update block (double2 steps)
 int fcg_update_blocks(int n) { return (int)(((n > 0 ? n : 1) + kUpdChunk - 1LL) / kUpdChunk); }
 
 __global__ void __launch_bounds__(kRB)

@@ -7,6 +7,12 @@
 
 namespace cwm {
 
+// Row walks of the tile and sliced kernels in predicated groups (1) or whole groups followed
+// by one entry per round trip (0, the earlier form, kept for measurement).
+#ifndef CWM_ROW_PRED
+#define CWM_ROW_PRED 1
+#endif
+
 template <class V>
 struct CsrView {
   int n = 0;
