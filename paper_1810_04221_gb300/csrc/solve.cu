@@ -1156,8 +1156,10 @@ int fcg_partial_blocks(int n) {
   const int cap = num_sms() * kDotsBlocksPerSm;
   return rb < cap ? rb : cap;
 }
+// double2 steps per thread of the FCG update: 2 (756 blocks on elasticity 64^3) gave a
+// 45.1 ms solve against 45.6 ms with 4 (378 blocks, two or three per SM); 1 measured as 2
 #ifndef CWM_UPD_STEPS
-#define CWM_UPD_STEPS 4
+#define CWM_UPD_STEPS 2
 #endif
 constexpr int kUpdChunk = 2 * CWM_UPD_STEPS * kRB;  // entries per fcg_update block (double2 steps)
 int fcg_update_blocks(int n) { return (int)(((n > 0 ? n : 1) + kUpdChunk - 1LL) / kUpdChunk); }
@@ -1258,7 +1260,7 @@ __global__ void __launch_bounds__(kBlock)
   const bool broken = scal[kFlags] != 0.0;  // breakdown: leave x, r, d, q as they were
   const double coef = scal[kCoef], step = scal[kStep];
   double rr = 0.0;
-  // the block owns kUpdChunk consecutive entries: four coalesced double2 steps per thread
+  // the block owns kUpdChunk consecutive entries: CWM_UPD_STEPS coalesced double2 steps per thread
   const long long base = (long long)blockIdx.x * kUpdChunk;
   if (!broken) {
 #pragma unroll
