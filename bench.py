@@ -473,8 +473,10 @@ def fp64_fractions(classes, n, nnz, nnz_nonzero, r_fma, r_div):
     """FP64 issue fraction of the FP64-bound classes: the time their FP64 operations take at
     the measured rates over their measured launch time.  spmv_dots: one FMA per stored entry
     and three per row (the dot products); weights@0 (the first sweep on the input operator):
-    per stored off-diagonal nonzero pair three multiplies and two adds (the division runs on
-    the integer pipes).  r_div is kept for callers; no class uses it now."""
+    two multiplies and two adds per evaluation (2a is an exponent increment and the division
+    runs on the integer pipes), once per stored off-diagonal nonzero pair on short-row
+    operators, once per such slot where rows average more than 32 slots (every slot is
+    evaluated in its own row).  r_div is kept for callers; no class uses it now."""
     out = []
     edges = max(nnz_nonzero - n, 0) / 2.0
     for c in classes:
@@ -482,8 +484,12 @@ def fp64_fractions(classes, n, nnz, nnz_nonzero, r_fma, r_div):
             t = (nnz + 3.0 * n) / r_fma
             what = "(nnz + 3n) FMA"
         elif c["kernel"] == "weights@0":
-            t = edges * 5.0 / r_fma
-            what = "per edge 5 FP64 ops (division on the integer pipes)"
+            if nnz > 32 * n:
+                t = 2.0 * edges * 4.0 / r_fma
+                what = "per stored off-diagonal nonzero slot 4 FP64 ops (division on the integer pipes)"
+            else:
+                t = edges * 4.0 / r_fma
+                what = "per edge 4 FP64 ops (division on the integer pipes)"
         else:
             continue
         out.append({"kernel": c["kernel"], "ops": what, "fp64_us": round(t * 1e6, 2),
