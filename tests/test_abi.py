@@ -60,6 +60,14 @@ def test_library_loads_and_host_calls_work(lib_path):
     # argument checks happen before any device work
     lib.amg_num_levels.restype = C.c_int
     assert lib.amg_num_levels(None) == -1
+    binding.load(lib_path)
+    L = binding.load()
+    ll = C.c_longlong()
+    assert L.cwm_copy(None, None, 16, None) == binding.AMG_ERR_INVALID_ARG
+    assert L.cwm_copy(C.c_void_p(8), C.c_void_p(16), -1, None) == binding.AMG_ERR_INVALID_ARG
+    assert L.cwm_copy(None, None, 0, None) == binding.AMG_OK  # nothing to copy: no device work
+    assert L.cwm_div_check(16, 1, None, C.byref(ll), None) == binding.AMG_ERR_INVALID_ARG
+    assert L.cwm_div_check(-1, 1, C.byref(ll), C.byref(ll), None) == binding.AMG_ERR_INVALID_ARG
 
 
 def test_struct_layout_matches_c(tmp_path):
