@@ -114,12 +114,13 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _traffic_for(kernel_class: str):
-    """DRAM bytes per launch from a committed ncu summary, or None if absent or stale."""
+def _traffic_for(kernel_class: str, workload: str | None):
+    """DRAM bytes per launch of a kernel class on a workload, from a committed ncu summary
+    (the file maps workload -> class -> capture), or None if absent or stale."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
-        e = d[kernel_class]
+        e = d[workload][kernel_class]
         src = os.path.join(ROOT, e["source"])
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if sha != e["source_sha256"]:
@@ -358,9 +359,9 @@ def run_cuda(args, rank, world, dist):
             roof = {"bound": "hbm", "kernel": dominant, "achieved": round(ach, 1), "peak": peak,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(ach / peak, 4),
                     "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": round(ach / NOMINAL_HBM_GBS, 4),
-                    "traffic": _traffic_for(dominant), "launches": nl,
+                    "traffic": _traffic_for(dominant, args.workload), "launches": nl,
                     "bytes_per_launch": byt / nl, "avg_launch_us": ms / nl * 1e3}
-            roof["classes"] = class_rooflines(trace_all, peak)
+            roof["classes"] = class_rooflines(trace_all, peak, args.workload)
             # the FP64-issue-bound classes against the FP64 rates measured on this GPU now
             try:
                 r_fma, r_div = B.cwm_fp64_rates()
@@ -450,7 +451,7 @@ def run_cuda(args, rank, world, dist):
         print(json.dumps(out))
 
 
-def class_rooflines(trace, peak):
+def class_rooflines(trace, peak, workload=None):
     """Per kernel class of one traced step: launches, algorithmic bytes per launch, average
     launch time and the fraction of the HBM peak those bytes reach."""
     out = []
@@ -462,7 +463,7 @@ def class_rooflines(trace, peak):
         row = {"kernel": e["name"], "launches": e["launches"], "total_ms": round(e["total_ms"], 4),
                "bytes_per_launch": round(bpl), "avg_launch_us": round(us, 2),
                "achieved_gbs": round(bpl / us * 1e-3, 1), "frac": round(bpl / us * 1e-3 / peak, 4)}
-        tr = _traffic_for(e["name"])
+        tr = _traffic_for(e["name"], workload)
         if tr is not None:
             row["traffic"] = tr
         out.append(row)

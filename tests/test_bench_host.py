@@ -57,23 +57,26 @@ def test_traffic_lookup_goes_stale_with_the_source(tmp_path, monkeypatch):
     entry = {"kernel": "k", "source": str(src), "dram_bytes_per_launch": 1.5e8,
              "source_sha256": hashlib.sha256(src.read_bytes()).hexdigest()}
     tf = tmp_path / "traffic.json"
-    tf.write_text(json.dumps({"spmv_dots": entry}))
+    tf.write_text(json.dumps({"poisson3d_128": {"spmv_dots": entry}}))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tf))
-    assert bench._traffic_for("spmv_dots") == 1.5e8
-    assert bench._traffic_for("jacobi@0") is None  # no capture for this class
+    assert bench._traffic_for("spmv_dots", "poisson3d_128") == 1.5e8
+    assert bench._traffic_for("jacobi@0", "poisson3d_128") is None  # no capture for this class
+    assert bench._traffic_for("spmv_dots", "lognormal_160") is None  # captured on another workload
     src.write_text("__global__ void k() { /* changed */ }\n")
-    assert bench._traffic_for("spmv_dots") is None  # the kernel changed since the capture
+    assert bench._traffic_for("spmv_dots", "poisson3d_128") is None  # the kernel changed since the capture
 
 
 def test_committed_traffic_entries_are_well_formed():
     with open(bench.TRAFFIC_FILE) as f:
         d = json.load(f)
-    assert "spmv_dots" in d
-    for cls, e in d.items():
-        assert set(e) >= {"kernel", "source", "source_sha256", "dram_bytes_per_launch", "profile"}
-        assert len(e["source_sha256"]) == 64 and e["dram_bytes_per_launch"] > 0
-        with open(f"{bench.ROOT}/{e['profile']}") as p:
-            assert e["kernel"] in p.read()
+    assert "spmv_dots_b3" in d["elasticity_64"]
+    for wl, classes in d.items():
+        assert wl in bench.WORKLOADS
+        for cls, e in classes.items():
+            assert set(e) >= {"kernel", "source", "source_sha256", "dram_bytes_per_launch", "profile"}
+            assert len(e["source_sha256"]) == 64 and e["dram_bytes_per_launch"] > 0
+            with open(f"{bench.ROOT}/{e['profile']}") as p:
+                assert e["kernel"] in p.read()
 
 
 def test_elasticity_workload_shape():
