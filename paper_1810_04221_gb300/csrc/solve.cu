@@ -882,7 +882,7 @@ __global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__re
     V acc = V(0);
     for (int k = s; k < e; ++k) {
       const int m = mlist[k];
-      acc += p[m] * r[m];
+      acc = fma(p[m], r[m], acc);
     }
     bc[I] = acc;
   }
