@@ -82,16 +82,9 @@ amg_status extract_diag(int n, const int *rp, const int *ci, const double *val, 
 // Sec. 2.2, C(A, v).  No FMA: every product and sum is an explicit round-to-nearest
 // intrinsic in the order ((2 a) v_a) v_b over ((a_aa v_a) v_a) + ((a_bb v_b) v_b),
 // a = min(i,j).  The quotient is the correctly rounded one, formed on the integer pipes
-// (div_rn_int), which leaves five binary64 operations per edge on the scarce FP64 pipe.
-//
-// Row blocks, evaluating each edge once.  A block of kWB
-// threads owns kWB consecutive rows.  Each row's thread finds where its upper part
-// (columns > i) starts, writes 0 into its diagonal slot, and the block packs the upper
-// slots of all its rows into one dense list (an exclusive scan of the per-row counts);
-// threads then take that list in chunks of kWC, so the FP64 work -- a pipe that retires
-// whole-warp instructions at a low rate on GB300 -- runs on full warps.  The thread that
-// evaluates slot (i, j) also stores the weight into the mirror slot (j, i), found by a
-// binary search in row j.
+// (div_rn_int), and 2 a is an exponent increment, which leaves four binary64 operations per
+// evaluation on the scarce FP64 pipe.
+
 // 2 a, exactly: the exponent field incremented when a is normal and 2 a finite (no FP64
 // instruction), else the multiply.
 __device__ __forceinline__ double twice_f64(double a) {
@@ -105,6 +98,15 @@ __device__ __forceinline__ double twice_f64(double a) {
 // row) 2.69 -> 2.35 ms of weights per setup; Poisson and lognormal (7 to 27 per row) lost
 // 25% and 16% with every slot evaluated.
 constexpr double kWeightsAllMean = 32.0;
+
+// Row blocks, evaluating each edge once.  A block of kWB
+// threads owns kWB consecutive rows.  Each row's thread finds where its upper part
+// (columns > i) starts, writes 0 into its diagonal slot, and the block packs the upper
+// slots of all its rows into one dense list (an exclusive scan of the per-row counts);
+// threads then take that list in chunks of kWC, so the FP64 work -- a pipe that retires
+// whole-warp instructions at a low rate on GB300 -- runs on full warps.  The thread that
+// evaluates slot (i, j) also stores the weight into the mirror slot (j, i), found by a
+// binary search in row j.
 constexpr int kWB = 256;
 constexpr int kWE = 8;
 constexpr int kWC = kWB * kWE;
@@ -286,8 +288,9 @@ amg_status edge_weights(int n, long long nnz, const int *rp, const int *ci, cons
   CWM_TRACE("weights", 4.0 * (n + 1) + 20.0 * nnz + 32.0 * n, s);
   k_vertex_dv<<<grid_for(n, 256, num_sms() * 8), 256, 0, s>>>(n, diag, v, dv_scratch);
   CWM_LAUNCH();
-  // lower slots without an upper partner (a pattern that is not symmetric) stay 0; a
-  // structurally symmetric pattern has every slot written, so the caller may skip this
+  // upper-triangle kernel: lower slots without an upper partner (a pattern that is not
+  // symmetric) stay 0; a structurally symmetric pattern has every slot written, so the
+  // caller may skip the clear.  The every-slot kernel writes every slot.
   if ((double)nnz > kWeightsAllMean * n) {
     k_edge_weights_all<<<(n + kWB - 1) / kWB, kWB, 0, s>>>(n, rp, ci, val, dv_scratch, v, w);
   } else {
