@@ -304,9 +304,10 @@ amg_status cwm_fp64_rates(double *fma_per_s, double *div_per_s, void *stream);
  * milliseconds about every half second; the kernel's did not), pageable host memory by
  * cudaMemcpyAsync (the call then waits for it), device to device by cudaMemcpyAsync.  At
  * least one of dst, src must be device memory (bytes = 0 does nothing and accepts any
- * pointers); the ranges must not overlap.  Ordered on
- * `stream`.  Errors: INVALID_ARG (NULL pointer, bytes < 0, no device side), CUDA.  The
- * paper has no counterpart. */
+ * pointers); the ranges must not overlap.  Ordered on `stream` and asynchronous for
+ * page-locked host memory: the caller leaves a host source unchanged, and reads a host
+ * destination only, after synchronising with the stream.  Errors: INVALID_ARG (NULL
+ * pointer, bytes < 0, no device side), CUDA.  The paper has no counterpart. */
 amg_status cwm_copy(void *dst, const void *src, int64_t bytes, void *stream);
 
 /* Self-check of the edge weights' quotient (Sec. 2.2: c = 1 - num / den is evaluated with a
