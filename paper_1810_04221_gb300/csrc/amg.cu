@@ -165,6 +165,7 @@ struct amg_hierarchy {
   // FCG vectors and reductions
   DBuf<double> r, w, d, vv, q, part, part2, scal;
   DBuf<double> bdev, xdev;  // device copies of a solve's host b and x (amg_pcg_solve)
+  DBuf<int> ap_stat;         // per level: nnz(A P) and its longest row, written by build_ap_level
   DBuf<unsigned> tick;  // last-block tickets of the fused reductions (kept at zero between launches)
   double t_setup_ms = 0.0, t_solve_ms = 0.0;
   Tracer trace;
@@ -436,55 +437,54 @@ bool wants_ap(const amg_hierarchy *h, const Level &L) {
 // Builds A P for the levels that take the coarse correction and their post-sweep through it
 // (cycle_level): with y = xs + P xc, b - A y = (b - A xs) - (A P) xc, and the residual
 // b - A xs is the one the restriction already formed, so the sweep streams A P (one entry per
-// aggregate met in a row) instead of A, and the separate prolongation pass goes.  Every
-// level's rows are grouped first, then one synchronisation reads the sizes, then the rows are
-// compacted.
-amg_status build_ap(amg_hierarchy *h) {
-  cudaStream_t s = h->stream;
-  std::vector<int> todo;
-  for (int k = 0; k + 1 < (int)h->lev.size(); ++k)
-    if (wants_ap(h, h->lev[k])) todo.push_back(k);
-  if (todo.empty()) return AMG_OK;
-  const size_t m = todo.size();
-  std::vector<DBuf<int>> ci_pad(m);
-  std::vector<DBuf<double>> val_pad(m);
-  DBuf<int> cnt, scan, stat;  // stat: per level, nnz(A P) and its longest row
-  int nmax = 0;
-  for (int k : todo) nmax = std::max(nmax, h->lev[k].n);
-  CWM_TRY(cnt.alloc((size_t)nmax + 1, s));
-  CWM_TRY(scan.alloc(scan_scratch_ints(nmax), s));
-  CWM_TRY(stat.alloc(2 * m, s));
-  CWM_CUDA(cudaMemsetAsync(stat.get(), 0, 2 * m * sizeof(int), s));
-  for (size_t q = 0; q < m; ++q) {
-    Level &L = h->lev[todo[q]];
-    LevelTag tag(todo[q]);
-    CWM_TRY(ci_pad[q].alloc(L.nnz, s));
-    CWM_TRY(val_pad[q].alloc(L.nnz, s));
-    CWM_TRY(L.ap_rp.alloc((size_t)L.n + 1, s));
-    CWM_TRY(ap_group(L.n, L.nnz, L.rp.get(), L.ci.get(), L.val.get(), L.agg.get(), L.p.get(), L.max_row,
-                     ci_pad[q].get(), val_pad[q].get(), cnt.get(), stat.get() + 2 * q + 1, s));
-    CWM_TRY(exclusive_scan(cnt.get(), L.ap_rp.get(), L.n, scan.get(), s));
-    CWM_CUDA(cudaMemcpyAsync(stat.get() + 2 * q, L.ap_rp.get() + L.n, sizeof(int), cudaMemcpyDeviceToDevice, s));
+// aggregate met in a row) instead of A, and the separate prolongation pass goes.  A level's
+// A P is built on the library's second stream as soon as the level's prolongator is known,
+// while the setup stream coarsens the next level: its rows are grouped at padded offsets,
+// scanned and compacted into arrays allocated at nnz(A) (an upper bound), so no host
+// synchronisation is needed; its sizes are read once, after the coarsening (ap_sizes).
+amg_status build_ap_level(amg_hierarchy *h, int k, cudaStream_t side) {
+  Level &L = h->lev[k];
+  LevelTag tag(k);
+  DBuf<int> ci_pad, cnt, scan;
+  DBuf<double> val_pad;
+  int *stat = h->ap_stat.get() + 2 * k;
+  CWM_TRY(ci_pad.alloc(L.nnz, side));
+  CWM_TRY(val_pad.alloc(L.nnz, side));
+  CWM_TRY(cnt.alloc((size_t)L.n + 1, side));
+  CWM_TRY(scan.alloc(scan_scratch_ints(L.n), side));
+  CWM_TRY(L.ap_rp.alloc((size_t)L.n + 1, side));
+  CWM_CUDA(cudaMemsetAsync(stat, 0, 2 * sizeof(int), side));
+  CWM_TRY(ap_group(L.n, L.nnz, L.rp.get(), L.ci.get(), L.val.get(), L.agg.get(), L.p.get(), L.max_row, ci_pad.get(),
+                   val_pad.get(), cnt.get(), stat + 1, side));
+  CWM_TRY(exclusive_scan(cnt.get(), L.ap_rp.get(), L.n, scan.get(), side));
+  CWM_CUDA(cudaMemcpyAsync(stat, L.ap_rp.get() + L.n, sizeof(int), cudaMemcpyDeviceToDevice, side));
+  // A P has at most as many entries as A: allocated at that bound, no synchronisation
+  CWM_TRY(L.ap_ci.alloc(L.nnz, side));
+  CWM_TRY(L.ap_val.alloc(L.nnz, side));
+  GalerkinWork gw;
+  gw.rpu = L.rp.get();
+  gw.ci_pad = ci_pad.get();
+  gw.val_pad = val_pad.get();
+  CWM_TRY(galerkin_compact(L.n, L.ap_rp.get(), L.ap_ci.get(), L.ap_val.get(), gw, side));
+  if (h->prm.vcycle_fp32) {
+    CWM_TRY(L.ap_val32.alloc(L.nnz, side));
+    CWM_TRY(to_float_count(stat, L.nnz, L.ap_val.get(), L.ap_val32.get(), side));
   }
-  std::vector<int> hs(2 * m);
-  CWM_CUDA(cudaMemcpyAsync(hs.data(), stat.get(), 2 * m * sizeof(int), cudaMemcpyDeviceToHost, s));
+  return AMG_OK;  // the scratch buffers are released in order on `side`
+}
+
+// After the side stream has been joined: the sizes of every A P built.
+amg_status ap_sizes(amg_hierarchy *h) {
+  const int nl = (int)h->lev.size();
+  std::vector<int> hs(2 * (size_t)nl);
+  CWM_CUDA(cudaMemcpyAsync(hs.data(), h->ap_stat.get(), 2 * sizeof(int) * (size_t)nl, cudaMemcpyDeviceToHost,
+                           h->stream));
   CWM_TRY(read_err(h, "amg_setup (A P)"));  // synchronises
-  const bool f32 = h->prm.vcycle_fp32 != 0;
-  for (size_t q = 0; q < m; ++q) {
-    Level &L = h->lev[todo[q]];
-    L.ap_nnz = hs[2 * q];
-    L.ap_max_row = hs[2 * q + 1];
-    CWM_TRY(L.ap_ci.alloc(L.ap_nnz, s));
-    CWM_TRY(L.ap_val.alloc(L.ap_nnz, s));
-    GalerkinWork gw;
-    gw.rpu = L.rp.get();
-    gw.ci_pad = ci_pad[q].get();
-    gw.val_pad = val_pad[q].get();
-    CWM_TRY(galerkin_compact(L.n, L.ap_rp.get(), L.ap_ci.get(), L.ap_val.get(), gw, s));
-    if (f32) {
-      CWM_TRY(L.ap_val32.alloc(L.ap_nnz, s));
-      CWM_TRY(to_float(L.ap_nnz, L.ap_val.get(), L.ap_val32.get(), s));
-    }
+  for (int k = 0; k < nl; ++k) {
+    Level &L = h->lev[k];
+    if (!L.ap_rp.get()) continue;
+    L.ap_nnz = hs[2 * k];
+    L.ap_max_row = hs[2 * k + 1];
   }
   return AMG_OK;
 }
@@ -1006,24 +1006,14 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
   L0.max_row = h->box.ints[5];
   CWM_TRY(l1_norms(L0.view64(), L0.dl1.get(), s));
 
-  while ((int)h->lev.size() < P.max_levels && h->lev.back().n > P.coarse_max) {
-    bool made = false;
-    const size_t before = h->lev.size();
-    CWM_TRY(coarsen_level(h, &made));
-    if (h->lev.size() == before) break;  // no pair at all: the current level is the coarsest
-    if (!made) break;
-    const Level &Fl = h->lev[h->lev.size() - 2], &Cl = h->lev.back();
-    if (P.stall_ratio > 0.0 && (double)Fl.n < P.stall_ratio * (double)Cl.n) break;
-  }
-  for (Level &L : h->lev) CWM_TRY(finish_level(h, L));
-  h->lev.back().nsweeps = 0;
   CWM_CUDA(cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking));
   CWM_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CWM_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
-  // The coarsest level's dense operator (FP64-bound) is built on the library's second stream
-  // while the setup stream builds the 3x3-block copy, A P and the sliced copies (latency-bound
-  // kernels); the setup stream waits for it before anything else is released or returned,
-  // on every path out of this function (Join runs before dense_tmp is freed).
+  // Work on the library's second stream (the A P of each level while the next level is
+  // coarsened, the coarsest level's dense operator while the setup stream builds the 3x3-block
+  // and sliced copies): the setup stream waits for it before anything else is released or
+  // returned, on every path out of this function (Join runs before the buffers it uses are
+  // freed).
   DBuf<double> dense_tmp;
   struct Join {
     cudaStream_t side = nullptr, main = nullptr;
@@ -1034,6 +1024,36 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
       cudaStreamWaitEvent(main, ev, 0);
     }
   } join;
+  cudaStream_t side = h->solve_stream;
+  CWM_TRY(h->ap_stat.alloc(2 * (size_t)P.max_levels, s));
+  while ((int)h->lev.size() < P.max_levels && h->lev.back().n > P.coarse_max) {
+    bool made = false;
+    const size_t before = h->lev.size();
+    CWM_TRY(coarsen_level(h, &made));
+    if (h->lev.size() == before) break;  // no pair at all: the current level is the coarsest
+    {  // the level just coarsened has its prolongator: its A P on the second stream
+      const int k = (int)h->lev.size() - 2;
+      if (wants_ap(h, h->lev[k])) {
+        CWM_CUDA(cudaEventRecord(h->ev_in, s));
+        CWM_CUDA(cudaStreamWaitEvent(side, h->ev_in, 0));
+        join.side = side;
+        join.main = s;
+        join.ev = h->ev_out;
+        CWM_TRY(build_ap_level(h, k, side));
+      }
+    }
+    if (!made) break;
+    const Level &Fl = h->lev[h->lev.size() - 2], &Cl = h->lev.back();
+    if (P.stall_ratio > 0.0 && (double)Fl.n < P.stall_ratio * (double)Cl.n) break;
+  }
+  for (Level &L : h->lev) CWM_TRY(finish_level(h, L));
+  h->lev.back().nsweeps = 0;
+  if (join.side) {  // the A P builds are done before their sizes are read
+    CWM_CUDA(cudaEventRecord(h->ev_out, side));
+    CWM_CUDA(cudaStreamWaitEvent(s, h->ev_out, 0));
+    join.side = nullptr;
+    CWM_TRY(ap_sizes(h));
+  }
   {
     Level &Lc = h->lev.back();
     LevelTag tag((int)h->lev.size() - 1);
@@ -1042,7 +1062,6 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
       CWM_TRY(Lc.xdense.alloc(nn, s));
       CWM_TRY(dense_tmp.alloc(nn, s));
       if (P.vcycle_fp32) CWM_TRY(Lc.xdense32.alloc(nn, s));
-      cudaStream_t side = h->solve_stream;
       CWM_CUDA(cudaEventRecord(h->ev_in, s));
       CWM_CUDA(cudaStreamWaitEvent(side, h->ev_in, 0));
       join.side = side;
@@ -1075,7 +1094,6 @@ static amg_status setup_impl(int n, int64_t nnz, const int32_t *rp, const int32_
                                cudaMemcpyHostToDevice, s));
     }
   }
-  CWM_TRY(build_ap(h));
   CWM_TRY(build_sell(h));
   // FCG work vectors
   CWM_TRY(h->r.alloc(n, s));

@@ -1377,6 +1377,18 @@ __global__ void k_to_double(long long n, const float *__restrict__ x, double *__
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
+// y = (float)x for the first *count entries (a count only the device knows yet)
+__global__ void k_to_float_count(const int *__restrict__ count, const double *__restrict__ x, float *__restrict__ y) {
+  const long long n = *count;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+amg_status to_float_count(const int *count, long long cap, const double *x, float *y, cudaStream_t s) {
+  if (cap <= 0) return AMG_OK;
+  k_to_float_count<<<grid_for(cap, kBlock, num_sms() * 8), kBlock, 0, s>>>(count, x, y);
+  CWM_LAUNCH();
+  return AMG_OK;
+}
 amg_status to_float(long long n, const double *x, float *y, cudaStream_t s) {
   if (n == 0) return AMG_OK;
   CWM_CUDA(launch_pdl(k_to_float, grid_for(n, kBlock, num_sms() * 8), kBlock, 0, s, n, x, y));

@@ -247,6 +247,8 @@ amg_status l1_norms(const CsrView<double> &A, double *d, cudaStream_t s);
 amg_status reciprocal(int n, const double *x, double *y, float *y32, cudaStream_t s);
 // float64 <-> float32 copies
 amg_status to_float(long long n, const double *x, float *y, cudaStream_t s);
+// the same for the first *count (device) of at most cap entries
+amg_status to_float_count(const int *count, long long cap, const double *x, float *y, cudaStream_t s);
 amg_status to_double(long long n, const float *x, double *y, cudaStream_t s);
 
 }  // namespace cwm
