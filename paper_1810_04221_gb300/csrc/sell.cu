@@ -23,7 +23,8 @@ constexpr int kSellWin = 256;  // rows sorted together (one block)
 // Entries per lane whose loads are in flight together in binary32 (4 in binary64), in
 // predicated groups: 8 measured 50.8 / 22.9 us on Q1 elasticity 64^3 levels 0 / 1 (A P),
 // 16 gave 53.0 / 27.0 (56 registers); whole groups with a one-at-a-time remainder gave
-// 59.0 / 31.0 at 16.
+// 59.0 / 31.0 at 16.  Loading the next group's columns one group ahead (as the tile walk
+// does) measured slower here: 52.4 / 23.2 us at 44 registers.
 #ifndef CWM_SELL_UNROLL32
 #define CWM_SELL_UNROLL32 8
 #endif

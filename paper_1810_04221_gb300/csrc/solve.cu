@@ -21,6 +21,9 @@ constexpr int kBlock = 256;
 #ifndef CWM_TILE_GROUP
 #define CWM_TILE_GROUP 4
 #endif
+#ifndef CWM_TILE_PREFETCH
+#define CWM_TILE_PREFETCH 1
+#endif
 template <class V, int T, bool NEG = false, bool SCALED = false>
 __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int *__restrict__ ci,
                                           const V *__restrict__ val, const V *__restrict__ x, long long row,
@@ -36,17 +39,32 @@ __device__ __forceinline__ V tile_row_dot(const int *__restrict__ rp, const int 
     // lane's products are added in ascending entry order
 #if CWM_ROW_PRED
     constexpr int G = CWM_TILE_GROUP;
+#if CWM_TILE_PREFETCH
+    // the next group's columns one group ahead: a group's value loads and x gathers go out
+    // together (elasticity level-2 A P sweep 14.3 -> 13.9 us, lognormal 160^3 41.5 -> 41.1 ms)
+    int jn[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) jn[u] = b + lane + u * T < e ? ci[b + lane + u * T] : 0;
+#endif
     for (int k = b + lane; k < e; k += G * T) {
       int jj[G];
       V aa[G], xx[G];
 #pragma unroll
       for (int u = 0; u < G; ++u) {
         const bool ok = k + u * T < e;
+#if CWM_TILE_PREFETCH
+        jj[u] = jn[u];
+#else
         jj[u] = ok ? ci[k + u * T] : 0;
+#endif
         aa[u] = ok ? val[k + u * T] : V(0);
       }
 #pragma unroll
       for (int u = 0; u < G; ++u) xx[u] = k + u * T < e ? xj(jj[u]) : V(0);
+#if CWM_TILE_PREFETCH
+#pragma unroll
+      for (int u = 0; u < G; ++u) jn[u] = k + (G + u) * T < e ? ci[k + (G + u) * T] : 0;
+#endif
 #pragma unroll
       for (int u = 0; u < G; ++u)
         if (k + u * T < e) s = fma(sg * aa[u], xx[u], s);
