@@ -1037,6 +1037,54 @@ __global__ void k_dense_sweep(int n, const int *__restrict__ rp, const int *__re
   Y[idx] = X[idx] + dinv[i] * (e - s);
 }
 
+// For symmetric A every X_k is symmetric: (I - D^{-1} A)^j D^{-1} = D^{-1/2} (I - S)^j D^{-1/2}
+// with S = D^{-1/2} A D^{-1/2}.  So a sweep computes the upper triangle (c >= i) and writes
+// each entry to both (i, c) and (c, i): half the FP64 multiply-adds, and every X_k exactly
+// symmetric.  A warp takes row i and 32 kDenseCpt consecutive columns, so each lane keeps
+// kDenseCpt independent FMA chains; each entry is still summed in ascending k.  Measured on
+// the 832-row coarsest level of Q1 elasticity 64^3 (20 sweeps, on the second stream beside
+// the last setup kernels): 1.90 -> 1.62 ms, setup 12.4-12.7 -> 12.0-12.1 ms.
+// CWM_DENSE_SYM=0 restores one thread per entry of the full square.
+#ifndef CWM_DENSE_SYM
+#define CWM_DENSE_SYM 1
+#endif
+constexpr int kDenseCpt = 2;
+__global__ void k_dense_sweep_sym(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                  const double *__restrict__ val, const double *__restrict__ dinv,
+                                  const double *__restrict__ X, double *__restrict__ Y) {
+  constexpr int W = 32 * kDenseCpt;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nch = (n + W - 1) / W;
+  if (warp >= (long long)n * nch) return;
+  const int i = (int)(warp / nch), c0 = (int)(warp % nch) * W;
+  if (c0 + W <= i) return;  // below the diagonal: written by the mirror stores
+  double sum[kDenseCpt];
+#pragma unroll
+  for (int u = 0; u < kDenseCpt; ++u) sum[u] = 0.0;
+  const int b = rp[i], e = rp[i + 1];
+#pragma unroll 4
+  for (int k = b; k < e; ++k) {
+    const double a = val[k];
+    const double *xr = X + (long long)ci[k] * n;
+#pragma unroll
+    for (int u = 0; u < kDenseCpt; ++u) {
+      const int c = c0 + lane + 32 * u;
+      if (c < n) sum[u] = fma(a, xr[c], sum[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kDenseCpt; ++u) {
+    const int c = c0 + lane + 32 * u;
+    if (c >= i && c < n) {
+      const long long ic = (long long)i * n + c;
+      const double y = X[ic] + dinv[i] * ((i == c ? 1.0 : 0.0) - sum[u]);
+      Y[ic] = y;
+      if (c != i) Y[(long long)c * n + i] = y;
+    }
+  }
+}
+
 amg_status dense_coarse_build(const CsrView<double> &A, const double *dinv, int sweeps, double *X, double *tmp,
                               cudaStream_t s) {
   const long long nn = (long long)A.n * A.n;
@@ -1049,10 +1097,15 @@ amg_status dense_coarse_build(const CsrView<double> &A, const double *dinv, int 
   // ping-pong so that the last sweep lands in X
   double *bufs[2] = {(sweeps % 2) ? X : tmp, (sweeps % 2) ? tmp : X};
   const int g = grid_for(nn, kBlock, 1 << 30);
+  const long long sym_warps = (long long)A.n * ((A.n + 32 * kDenseCpt - 1) / (32 * kDenseCpt));
+  const int g_sym = grid_for(sym_warps * 32, kBlock, 1 << 30);
   for (int k = 0; k < sweeps; ++k) {
     const double *src = bufs[(k + 1) & 1];
     double *dst = bufs[k & 1];
-    k_dense_sweep<<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, src, dst, k == 0);
+    if (CWM_DENSE_SYM && k > 0)
+      k_dense_sweep_sym<<<g_sym, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, src, dst);
+    else
+      k_dense_sweep<<<g, kBlock, 0, s>>>(A.n, A.rp, A.ci, A.val, dinv, src, dst, k == 0);
     CWM_LAUNCH();
   }
   return AMG_OK;
