@@ -54,8 +54,9 @@ typedef struct {
                            (FCG recurrences stay float64); 0: all float64 (default 0) */
   int check_input;      /* 1: amg_setup verifies CSR structure and bit symmetry of A on
                            the device before coarsening (default 1).  0: the caller
-                           vouches for both; the coarse operators' edge weights then
-                           rely on the symmetric pattern (an unchecked non-symmetric
+                           vouches for both; the coarse operators' edge weights and
+                           the coarsest level's dense operator (built on its upper
+                           triangle) then rely on symmetry (an unchecked non-symmetric
                            input gives an undefined, though terminating, hierarchy) */
   int keep_sweeps;      /* 1: keep every sweep's matching for amg_sweep_mate (default 0) */
   int64_t loop_cap;     /* cap on iterations of any one device retry loop or wait (Suitor
