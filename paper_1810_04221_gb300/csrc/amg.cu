@@ -419,7 +419,7 @@ constexpr int kApMaxRow = 1024;
 // 16.24 ms, lognormal 44.9 -> 45.5 ms), so short-row levels keep the separate passes.
 constexpr double kApAutoMinMean = 16.0;
 
-// Whether level L gets A P (see build_ap).
+// Whether level L gets A P (built by build_ap_level).
 bool wants_ap(const amg_hierarchy *h, const Level &L) {
   const amg_params &P = h->prm;
   if (!L.agg.get() || P.coupled_post < 0 || P.post_sweeps != 1 || L.max_row > kApMaxRow || L.nnz == 0) return false;
