@@ -55,6 +55,43 @@ def test_l1_jacobi_norms_and_contraction():
     assert np.abs((xs - x3) - np.linalg.matrix_power(E, 3) @ (xs - x0)).max() < 1e-12
 
 
+@pytest.mark.parametrize("kind", ["diff", "p2", "rand"])
+def test_coarsest_sweeps_map_is_symmetric(kind):
+    """The coarsest level's 20 l1-Jacobi sweeps from zero are the linear map
+    B = sum_{k<20} (I - D^-1 A)^k D^-1, and B is symmetric for symmetric A (it equals
+    D^-1/2 p(D^-1/2 A D^-1/2) D^-1/2); a GPU may therefore build B on one triangle.  B is
+    taken column by column from the oracle's own sweeps on unit vectors."""
+    (rp, ci, val), H = _hier(kind)
+    k = H.nl - 1
+    A, _, D = _dense_levels(H)
+    Ac, dc = A[k], D[k]
+    nc = Ac.shape[0]
+    assert 1 < nc <= 60
+    Bm = np.empty((nc, nc))
+    for c in range(nc):
+        e = np.zeros(nc)
+        e[c] = 1.0
+        Bm[:, c] = H.l1_jacobi(k, e, np.zeros(nc), 20)
+    scale = np.abs(Bm).max()
+    assert np.abs(Bm - Bm.T).max() <= 1e-13 * scale
+    M = np.eye(nc) - Ac / dc[:, None]
+    closed, term = np.zeros((nc, nc)), np.diag(1.0 / dc)
+    for _ in range(20):
+        closed += term
+        term = M @ term
+    assert np.abs(Bm - closed).max() <= 1e-13 * scale
+    # not a property every sweep count of every matrix shares: a nonsymmetric A breaks it
+    An = Ac.copy()
+    i, j = next((i, j) for i, j in zip(*np.nonzero(Ac)) if i != j)
+    An[i, j] *= 1.5
+    Mn = np.eye(nc) - An / dc[:, None]
+    Bn, term = np.zeros((nc, nc)), np.diag(1.0 / dc)
+    for _ in range(20):
+        Bn += term
+        term = Mn @ term
+    assert np.abs(Bn - Bn.T).max() > 1e-6 * np.abs(Bn).max()
+
+
 @pytest.mark.parametrize("kind,pre,post", [("diff", 1, 1), ("p2", 1, 1), ("rand", 2, 1)])
 def test_vcycle_error_propagation_identity(kind, pre, post):
     """I - B A = (I - D^-1 A)^post (I - P B_c P^T A) (I - D^-1 A)^pre per level and
